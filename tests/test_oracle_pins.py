@@ -1,0 +1,391 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test ties an oracle function to something other than itself: a table or
+value printed in the paper (tests/golden/), a closed form, an exact invariant
+(mass, momentum budget), a special case with a known answer (Poiseuille flow,
+free-slip uniform acceleration), or an asymptote of the wall law.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rows(name):
+    with open(os.path.join(GOLDEN, name)) as fh:
+        return [ln.split() for ln in fh if ln.strip() and not ln.startswith("#")]
+
+
+# ------------------------------------------------------------------ tables --
+
+def test_table_a1_velocities(oracle_lib):
+    e, w, opp, mir = oracle_lib.table()
+    for row in _rows("table_a1_d3q19.txt"):
+        a, ex, ey, ez = map(int, row)
+        assert tuple(e[a]) == (ex, ey, ez), a
+
+
+def test_eq10_momentum_sums(oracle_lib):
+    """Eq. 10b-d: sum_a e_a f_a with the table must equal the printed signed sums."""
+    e, _, _, _ = oracle_lib.table()
+    rng = np.random.default_rng(0)
+    f = rng.random(19)
+    for row in _rows("eq10_momentum_sums.txt"):
+        comp = "xyz".index(row[0])
+        printed = sum(math.copysign(1.0, int(t) if t != "-0" else -1) * f[abs(int(t))]
+                      for t in row[1:])
+        assert abs(float(e[:, comp] @ f) - printed) < 1e-15
+
+
+def test_opposite_and_mirror(oracle_lib):
+    e, _, opp, mir = oracle_lib.table()
+    for a in range(19):
+        assert tuple(e[opp[a]]) == tuple(-e[a])
+        assert tuple(e[mir[a]]) == (e[a][0], -e[a][1], e[a][2])
+
+
+def test_eq14_specular_partners(oracle_lib):
+    """The partners of Eq. 14a,b are the y-mirror images of the reflected directions."""
+    _, _, _, mir = oracle_lib.table()
+    for refl, partner, _sign, _comp in _rows("eq14_wfb_partners.txt"):
+        assert mir[int(refl)] == int(partner)
+
+
+# ------------------------------------------------------------- equilibrium --
+
+@pytest.mark.parametrize("seed", range(5))
+def test_feq_moments(oracle_lib, seed):
+    """sum feq = rho, sum e feq = rho u, sum e e feq = rho (I/3 + u u)."""
+    e, _, _, _ = oracle_lib.table()
+    rng = np.random.default_rng(seed)
+    rho = 0.9 + 0.2 * rng.random()
+    u = 0.1 * (rng.random(3) - 0.5)
+    fe = oracle_lib.feq(rho, u)
+    assert abs(fe.sum() - rho) < 1e-15
+    assert np.allclose(e.T @ fe, rho * u, rtol=0, atol=1e-16)
+    second = np.einsum("ai,aj,a->ij", e, e, fe)
+    assert np.allclose(second, rho * (np.eye(3) / 3.0 + np.outer(u, u)), rtol=0, atol=1e-16)
+
+
+def test_feq_rest_weights(oracle_lib):
+    """At rest feq = w: 1/3, 1/18 on the axes, 1/36 on the diagonals."""
+    fe = oracle_lib.feq(1.0, [0, 0, 0])
+    assert fe[0] == 1.0 / 3.0
+    assert all(fe[a] == 1.0 / 18.0 for a in range(1, 7))
+    assert all(fe[a] == 1.0 / 36.0 for a in range(7, 19))
+
+
+# -------------------------------------------------------------------- Guo --
+
+@pytest.mark.parametrize("seed", range(4))
+def test_guo_moments(oracle_lib, seed):
+    """sum F_a = 0, sum e F_a = (1 - 1/2tau) F, sum ee F_a = (1 - 1/2tau)(uF + Fu)."""
+    e, _, _, _ = oracle_lib.table()
+    rng = np.random.default_rng(10 + seed)
+    tau = 0.5 + rng.random()
+    u = 0.1 * (rng.random(3) - 0.5)
+    F = 1e-3 * (rng.random(3) - 0.5)
+    Fa = oracle_lib.guo(tau, u, F)
+    k = 1.0 - 0.5 / tau
+    assert abs(Fa.sum()) < 1e-18
+    assert np.allclose(e.T @ Fa, k * F, rtol=1e-13, atol=1e-19)
+    second = np.einsum("ai,aj,a->ij", e, e, Fa)
+    assert np.allclose(second, k * (np.outer(u, F) + np.outer(F, u)), rtol=1e-12, atol=1e-19)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_collision_mass_and_momentum(oracle_lib, seed):
+    """One BGK + Guo collision conserves mass and adds exactly F of momentum."""
+    e, _, _, _ = oracle_lib.table()
+    rng = np.random.default_rng(20 + seed)
+    f = oracle_lib.feq(1.0, 0.05 * rng.random(3)) * (1 + 0.05 * (rng.random(19) - 0.5))
+    F = np.array([3e-6, -1e-6, 2e-6])
+    fs, rho, u, tau = oracle_lib.collide(f, 0.52, 0.1, F)
+    assert abs(fs.sum() - f.sum()) < 1e-15
+    assert np.allclose(e.T @ (fs - f), F, rtol=1e-9, atol=1e-17)
+    assert tau >= 0.52
+
+
+# ------------------------------------------------------------- Smagorinsky --
+
+def _chapman_enskog_f(oracle_lib, rho, u, S, tau):
+    """f = feq + f_neq with the first-order non-equilibrium of a flow with strain
+    rate S relaxed at tau: f_neq_a = -(tau w_a rho / c_s^2)(e_a e_a - c_s^2 I):S."""
+    e, w, _, _ = oracle_lib.table()
+    cs2 = 1.0 / 3.0
+    qa = np.einsum("ai,aj->aij", e, e) - cs2 * np.eye(3)[None]
+    fneq = -(tau * w * rho / cs2) * np.einsum("aij,ij->a", qa, S)
+    return oracle_lib.feq(rho, u) + fneq
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_smagorinsky_matches_eddy_viscosity(oracle_lib, seed):
+    """Build a cell whose non-equilibrium part belongs to strain rate S relaxed at
+    a chosen tau_t; choose C_s so that c_s^2 (tau_t - tau0) = C_s^2 |S| with
+    |S| = sqrt(2 S:S). The oracle's closure must return tau_t."""
+    rng = np.random.default_rng(30 + seed)
+    A = 1e-3 * (rng.random((3, 3)) - 0.5)
+    S = 0.5 * (A + A.T)
+    S -= np.trace(S) / 3.0 * np.eye(3)          # incompressible strain
+    rho, tau0 = 1.0 + 0.01 * rng.random(), 0.5 + 0.05 * rng.random()
+    tau_t = tau0 + 0.2 * rng.random()
+    smag = math.sqrt(2.0 * float(np.sum(S * S)))
+    cs = math.sqrt((tau_t - tau0) / 3.0 / smag)
+    f = _chapman_enskog_f(oracle_lib, rho, np.zeros(3), S, tau_t)
+    fe = oracle_lib.feq(rho, np.zeros(3))
+    pi = oracle_lib.pi_neq(f, fe)
+    assert np.allclose(pi, -2.0 * rho / 3.0 * tau_t * S, rtol=1e-12, atol=1e-18)
+    assert abs(oracle_lib.tau_eff(tau0, cs, rho, pi) - tau_t) < 1e-12
+
+
+def test_smagorinsky_off(oracle_lib):
+    pi = np.arange(9, dtype=float) * 1e-4
+    assert oracle_lib.tau_eff(0.53, 0.0, 1.0, pi) == 0.53
+
+
+# ---------------------------------------------------------------- Spalding --
+
+def test_spalding_viscous_limit(oracle_lib):
+    """Eq. 16: y+ - u+ = e^{-kB} sum_{k>=4} (k u+)^k / k!; its leading term is
+    e^{-kB} (k u+)^4 / 24, so the bracket's first four terms cancel exactly."""
+    kap, B = 0.41, 5.5
+    for up in (1e-2, 3e-2, 0.1):
+        lead = math.exp(-kap * B) * (kap * up) ** 4 / 24.0
+        got = oracle_lib.spalding_yplus(up) - up
+        assert abs(got - lead) <= 0.05 * lead + 1e-17
+
+
+def test_spalding_log_limit(oracle_lib):
+    """For large u+ Eq. 16 tends to the log law u+ = ln(y+)/kappa + B."""
+    kap, B = 0.41, 5.5
+    for up in (40.0, 60.0):
+        yp = oracle_lib.spalding_yplus(up)
+        assert abs(math.log(yp) / kap + B - up) < 2e-3 * up
+
+
+@pytest.mark.parametrize("yplus", np.logspace(-3, 4, 29))
+def test_spalding_newton_round_trip(oracle_lib, yplus):
+    """u+ -> y+ (Eq. 16) -> R = u+ y+ -> Newton -> u+ recovered to 1e-10."""
+    # find u+ for this y+ by bisection on the explicit Eq. 16 (independent path)
+    lo, hi = 0.0, 100.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if oracle_lib.spalding_yplus(mid) < yplus:
+            lo = mid
+        else:
+            hi = mid
+    up_true = 0.5 * (lo + hi)
+    R = up_true * oracle_lib.spalding_yplus(up_true)
+    up, n, it = oracle_lib.spalding_newton(R)
+    assert abs(up - up_true) <= 1e-10 * max(1.0, up_true)
+    assert n < 1000
+    # Newton from the laminar guess sqrt(R) never undershoots and decreases monotonically
+    assert it[0] == pytest.approx(math.sqrt(R))
+    assert np.all(np.diff(it) <= 1e-12 * it[0])
+    assert np.all(it >= up_true * (1 - 1e-12))
+
+
+def test_wfb_stress_direction_and_law(oracle_lib):
+    """tau_w opposite to the tangential velocity (Eq. 15) and consistent with Eq. 16-17."""
+    rng = np.random.default_rng(5)
+    nu, y1 = 1e-4, 1.0
+    for _ in range(20):
+        rho = 1 + 0.01 * rng.random()
+        u = np.array([0.05 * rng.random() - 0.01, 0.01 * rng.random(), 0.02 * rng.random() - 0.01])
+        tw = oracle_lib.wfb_stress(rho, u, nu=nu, y1=y1)
+        ut = math.hypot(u[0], u[2])
+        tmag = math.hypot(*tw)
+        assert np.allclose(tw / tmag, -np.array([u[0], u[2]]) / ut, atol=1e-14)
+        utau = math.sqrt(tmag / rho)
+        yplus = y1 * utau / nu
+        assert abs(oracle_lib.spalding_yplus(ut / utau) - yplus) < 1e-9 * yplus
+    assert np.all(oracle_lib.wfb_stress(1.0, [0.0, 0.02, 0.0]) == 0.0)
+
+
+# ----------------------------------------------------------- lattice level --
+
+def _seeded(oracle_lib, nx, ny, nz, wall, tau=0.52, cs=0.1, force=(2.2e-7, 0, 0),
+            amp=4e-3, seed=7, stats_every=0):
+    L = oracle_lib.Lattice(nx, ny, nz, tau, cs, force, wall, stats_every=stats_every)
+    j = np.arange(ny)
+    L.init_channel(0.03 * np.minimum(j + 0.5, ny - j - 0.5) / (ny / 2), amp, seed)
+    return L
+
+
+@pytest.mark.parametrize("wall", [0, 1, 2])
+def test_mass_conserved(oracle_lib, wall):
+    L = _seeded(oracle_lib, 12, 8, 10, wall)
+    m0 = math.fsum(L.populations().ravel())
+    for _ in range(6):
+        L.step(1)
+        m = math.fsum(L.populations().ravel())
+        assert abs(m - m0) <= 1e-12 * m0
+
+
+@pytest.mark.parametrize("wall", [0, 1, 2])
+def test_momentum_budget(oracle_lib, wall):
+    """Eq. 9 / 12b summed: each step the x and z momentum change by N F plus the
+    tangential stress the walls exert (as reported per wall cell)."""
+    e, _, _, _ = oracle_lib.table()
+    F = np.array([2.2e-7, 0.0, -1.1e-7])
+    L = _seeded(oracle_lib, 12, 8, 10, wall, force=F, amp=6e-3)
+
+    def mom():
+        f = L.populations().reshape(19, -1)
+        return np.array([math.fsum((e[:, c][:, None] * f).ravel()) for c in range(3)])
+
+    p0 = mom()
+    for _ in range(5):
+        L.step(1)
+        p1 = mom()
+        tw = L.wall_stress()
+        for c, comp in ((0, 0), (2, 1)):
+            expect = L.n * F[c] + math.fsum(tw[..., comp].ravel())
+            assert abs((p1[c] - p0[c]) - expect) <= 1e-13 + 1e-9 * abs(expect), (wall, c)
+        if wall == 1:
+            assert np.any(tw != 0.0)
+        if wall == 2:
+            assert np.all(tw == 0.0)
+        p0 = p1
+
+
+def test_freeslip_uniform_acceleration(oracle_lib):
+    """A uniform field between free-slip walls stays uniform; u(t) = u(0) + F t."""
+    nx, ny, nz = 6, 5, 4
+    F = np.array([3e-5, 0.0, -2e-5])
+    L = oracle_lib.Lattice(nx, ny, nz, 0.6, 0.1, F, 2)
+    u0 = np.array([0.02, 0.0, 0.01])
+    fe = oracle_lib.feq(1.0, u0)
+    L.set_populations(np.repeat(fe[:, None], L.n, axis=1))
+    for t in range(1, 11):
+        L.step(1)
+        rho, u = L.moments()
+        # round-off only: a few ulp per step
+        assert np.allclose(rho, 1.0, rtol=0, atol=4e-16 * t)
+        expect = u0 + F * t + 0.5 * F      # moments carry the F/2 shift
+        for c in range(3):
+            assert np.allclose(u[c], expect[c], rtol=0, atol=2e-16 * t)
+
+
+def test_freeslip_keeps_layers_identical(oracle_lib):
+    """A y-independent, y-symmetric field between free-slip walls evolves exactly as
+    in a y-periodic box: every layer stays identical up to round-off (the y-momentum
+    sum is not exactly zero in floating point). A wrong x/z shift in the specular
+    map would make the wall layers differ from the interior at O(u)."""
+    nx, ny, nz = 8, 6, 10
+    L = oracle_lib.Lattice(nx, ny, nz, 0.55, 0.1, (1e-6, 0, 0), 2)
+    x = np.arange(nx)
+    z = np.arange(nz)
+    f = np.zeros((19, nz, ny, nx))
+    for k in range(nz):
+        for i in range(nx):
+            u = [0.03 * math.sin(2 * math.pi * z[k] / nz), 0.0, 0.02 * math.cos(2 * math.pi * x[i] / nx)]
+            f[:, k, :, i] = oracle_lib.feq(1.0, u)[:, None]
+    L.set_populations(f)
+    L.step(15)
+    g = L.populations()
+    for j in range(1, ny):
+        assert np.max(np.abs(g[:, :, j, :] - g[:, :, 0, :])) < 1e-15
+    assert not np.allclose(g, f)
+
+
+def _poiseuille(oracle_lib, ny, tau, steps, F=1e-6):
+    nu = (tau - 0.5) / 3.0
+    y = np.arange(ny) + 0.5
+    exact = F / (2 * nu) * y * (ny - y)
+    L = oracle_lib.Lattice(1, ny, 1, tau, 0.0, (F, 0, 0), 0)
+    f = np.stack([oracle_lib.feq(1.0, [ux, 0, 0]) for ux in exact], axis=1)
+    L.set_populations(f.reshape(19, -1))
+    L.step(steps)
+    _, u = L.moments()
+    ux = u[0, 0, :, 0]
+    return ux, exact, L
+
+
+def test_poiseuille_bb_magic_tau(oracle_lib):
+    """BGK with halfway bounce-back reproduces the parabola exactly when
+    (tau - 1/2)^2 = 3/16 (the wall sits exactly half a link out)."""
+    tau = 0.5 + math.sqrt(3.0) / 4.0
+    ux, exact, L = _poiseuille(oracle_lib, 16, tau, 6000)
+    assert np.max(np.abs(ux - exact)) <= 1e-10 * np.max(exact)
+    # force balance: both walls together take N F per column
+    tw = L.wall_stress()
+    assert abs(tw[..., 0].sum() + 16 * 1e-6) < 1e-12
+
+
+def test_poiseuille_bb_tau052(oracle_lib):
+    """At the parity case's tau0 = 0.52 the relative L2 error is below 1e-3 at
+    H = 48 (the BGK halfway-wall slip error falls as 1/H^2: 1.3e-3 at H = 32)."""
+    ux, exact, _ = _poiseuille(oracle_lib, 48, 0.52, 180000)
+    err = np.linalg.norm(ux - exact) / np.linalg.norm(exact)
+    assert err <= 1e-3
+
+
+def test_wfb_delta_f_roundoff(oracle_lib):
+    """Eq. B-1: the WFB reassignment keeps the population sum of every wall cell;
+    in floating point only round-off (relative to mean f) remains."""
+    L = _seeded(oracle_lib, 16, 8, 12, 1, amp=6e-3)
+    nonzero = 0
+    for _ in range(10):
+        L.step(1)
+        d = L.wall_delta_f()
+        assert np.all(np.abs(d) <= 1e-14 * (1.0 / 19.0) * 19)
+        nonzero += int(np.count_nonzero(d))
+    L2 = _seeded(oracle_lib, 16, 8, 12, 2)
+    L2.step(3)
+    assert np.all(L2.wall_delta_f() == 0.0)
+
+
+def test_plane_stats_match_moments(oracle_lib):
+    """The accumulated plane statistics equal sums of the moments at the sample times."""
+    L = _seeded(oracle_lib, 8, 6, 6, 1, stats_every=2)
+    acc = np.zeros((6, 11))
+    for t in range(6):
+        if t % 2 == 0:
+            rho, u = L.moments()
+            cols = [rho, u[0], u[1], u[2], u[0] ** 2, u[1] ** 2, u[2] ** 2, u[0] * u[1],
+                    rho * u[0], rho * u[1], rho * u[2]]
+            for k, c in enumerate(cols):
+                acc[:, k] += c.sum(axis=(0, 2))
+        L.step(1)
+    stats, wstats, ns = L.plane_stats()
+    assert ns == 3
+    assert np.allclose(stats, acc, rtol=1e-12, atol=1e-15)
+
+
+def test_init_channel_field(oracle_lib):
+    """f = feq(1, u0) with u0 = mean profile + uniform noise from SplitMix64."""
+    nx, ny, nz = 4, 6, 3
+    L = oracle_lib.Lattice(nx, ny, nz, 0.52, 0.1, (0, 0, 0), 1)
+    prof = np.linspace(0.01, 0.02, ny)
+    amp, seed = 1e-3, 99
+    L.init_channel(prof, amp, seed)
+    rho, u = L.moments()
+    assert np.allclose(rho, 1.0, atol=1e-15)
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                idx = (k * ny + j) * nx + i
+                for c in range(3):
+                    r = oracle_lib.uniform(seed, idx * 3 + c)
+                    assert 0.0 <= r < 1.0
+                    expect = (prof[j] if c == 0 else 0.0) + (2 * r - 1) * amp
+                    assert abs(u[c, k, j, i] - expect) < 1e-16
+
+
+def test_splitmix64_reference_vectors(oracle_lib):
+    gamma = 0x9E3779B97F4A7C15
+    for row in _rows("splitmix64.txt"):
+        state = int(row[0])
+        for out in row[1:]:
+            assert oracle_lib.splitmix64(state) == int(out)
+            state = (state + gamma) & 0xFFFFFFFFFFFFFFFF
+
+
+def test_table1_first_layer_convention():
+    """y1 = 1 lattice spacing reproduces Table 1's printed first-layer y+."""
+    for _case, re_tau, d_over_dx, yplus in _rows("table1_first_layer.txt"):
+        assert round(float(re_tau) * 1.0 / float(d_over_dx)) == int(yplus)
