@@ -1,0 +1,358 @@
+"""Throughput of the fused WFB LBM-LES channel step on GB300 (MLUPS).
+
+One step = one pass of the whole hot path (gather/stream, moments, BGK +
+Smagorinsky + Guo force, WFB wall layers with the Spalding Newton solve,
+store) over every cell of the channel. The headline line is the FP32 channel
+256 x 64 x 128 (Re_tau 640, WFB walls, seeded log-law + 10% noise); extra
+variants (larger grid, FP16-shifted storage) are reported in the same line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun each rank runs an independent replica on its own GPU
+(replicas only: the channels share nothing); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2009_04352_gb300 import workload  # noqa: E402
+
+METRIC = "MLUPS and % of HBM roofline, FP32 vs FP16-storage vs batched, at stated err"
+BYTES_PER_LUP = {0: 152, 1: 76}     # 19 reads + 19 writes, FP32 / FP16 storage
+FALLBACK_HBM_GBS = 6800.0
+
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# dominant kernel from one ncu capture, keyed by workload; None until measured
+# for the current kernel build.
+NCU_TRAFFIC = {}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16"])
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            with open(path) as fh:
+                d = json.load(fh)
+            for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if k in d:
+                    v = d[k]
+                    if isinstance(v, dict):
+                        v = v.get("value", v.get("gbs"))
+                    return float(v), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def time_channel(case, precision, steps, warmup, stream, clocks=None):
+    """Device time of `steps` steps (CUDA events on the handle's stream)."""
+    import torch
+    from paper_2009_04352_gb300 import lbm
+
+    with torch.cuda.stream(stream):
+        ch = lbm.Channel.from_case(case, precision=precision, stream=stream.cuda_stream)
+        ch.init_channel(workload.u_mean_profile(case), workload.noise_amplitude(case), case.seed)
+        ch.step(warmup)
+        ch.sync()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ctx = clocks if clocks is not None else _Null()
+        with ctx:
+            ev0.record(stream)
+            ch.step(steps)
+            ev1.record(stream)
+            ev1.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        cons = ch.conservation()
+        finite = bool(np.all(np.isfinite(cons)))
+        ch.close()
+    return ms, finite
+
+
+class _Null:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        return False
+
+
+def e2e_channel(case, precision, steps, stream):
+    """Same metric end to end through the public API with host buffers: upload
+    the initial field from pinned host memory, run the steps with plane
+    statistics sampled every 10 steps, read the moments and statistics back."""
+    import torch
+    from paper_2009_04352_gb300 import lbm
+
+    f0 = workload_initial_populations(case)
+    pinned = torch.from_numpy(f0).pin_memory()
+    host_f = pinned.numpy()
+    rho = torch.empty((case.nz, case.ny, case.nx), dtype=torch.float32).pin_memory().numpy()
+    u = torch.empty((3, case.nz, case.ny, case.nx), dtype=torch.float32).pin_memory().numpy()
+    with torch.cuda.stream(stream):
+        ch = lbm.Channel.from_case(case, precision=precision, stream=stream.cuda_stream)
+        ch.set_populations(host_f)      # warm the staging path once
+        ch.step(10)
+        ch.sync()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ch.set_populations(host_f)
+        ch.set_stats_every(10)
+        ch.step(steps)
+        lbm.lbm_moments(ch.handle, rho.ctypes.data, u.ctypes.data, 0)
+        st, w, ns = ch.plane_stats()
+        t1 = time.perf_counter()
+        ch.close()
+    h2d = f0.nbytes
+    d2h = rho.nbytes + u.nbytes + st.nbytes + w.nbytes
+    return (t1 - t0) * 1e3, h2d, d2h
+
+
+def workload_initial_populations(case):
+    """Initial populations f = f^eq(1, u0) of the seeded channel, generated on
+    the device by the library and copied back once (outside any timed region)."""
+    from paper_2009_04352_gb300 import lbm
+    ch = lbm.Channel.from_case(case, stream=0)
+    ch.init_channel(workload.u_mean_profile(case), workload.noise_amplitude(case), case.seed)
+    f = ch.populations()
+    ch.close()
+    return f
+
+
+def cpu_baseline(case, budget_s=12.0):
+    """The FP64 oracle as it stands, single-threaded, on a bounded sample."""
+    import oracle
+    L = oracle.Lattice.from_case(case)
+    L.init_channel(workload.u_mean_profile(case), workload.noise_amplitude(case), case.seed)
+    t0 = time.perf_counter()
+    L.step(1)
+    one = time.perf_counter() - t0
+    n = max(1, int(budget_s / max(one, 1e-6)) - 1)
+    t0 = time.perf_counter()
+    L.step(n)
+    dt = time.perf_counter() - t0
+    L.close()
+    return {"value": case.cells * n / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"FP64 oracle, {case.nx}x{case.ny}x{case.nz} WFB channel, {n} steps "
+                      f"after 1 warm-up step ({dt:.1f} s)"}
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def main_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    case = workload.CASES[args.workload]
+    import oracle
+    L = oracle.Lattice.from_case(case)
+    L.init_channel(workload.u_mean_profile(case), workload.noise_amplitude(case), case.seed)
+    # each "step" of this arm is a bounded sample: one oracle step of the workload
+    L.step(max(0, min(args.warmup, 1)))
+    steps = max(1, min(args.steps, 8))
+    t0 = time.perf_counter()
+    L.step(steps)
+    dt = time.perf_counter() - t0
+    L.close()
+    val = case.cells * steps / dt / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": steps, "warmup": min(args.warmup, 1), "ms_per_step": dt * 1e3 / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": case.name, "cells": case.cells},
+            "cpu_baseline": {"value": val, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                             "sample": f"FP64 oracle, {steps} steps of {case.name} (cpu: {cpu_model()})"},
+            "e2e": {"value": val, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return main_reference(args)
+
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    from paper_2009_04352_gb300 import lbm
+
+    precision = lbm.FP32 if args.precision == "fp32" else lbm.FP16_SHIFTED
+    case = workload.CASES[args.workload]
+    stream = torch.cuda.Stream()
+    peak, peak_src = measured_peaks()
+
+    clocks = ClockSampler(local)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    ms, finite = time_channel(case, precision, args.steps, args.warmup, stream, clocks)
+    torch.cuda.synchronize()
+    if pg:
+        t = torch.tensor([ms], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+        pg.barrier()
+    total_cells = case.cells * world
+    mlups = total_cells * args.steps / (ms * 1e-3) / 1e6
+    per_gpu_mlups = case.cells * args.steps / (ms * 1e-3) / 1e6
+    kernel_ms = ms / args.steps
+    achieved = BYTES_PER_LUP[precision] * case.cells / (kernel_ms * 1e-3) / 1e9
+
+    e2e = None
+    if not args.no_e2e:
+        e2e_steps = min(args.steps, 2000)
+        e_ms, h2d, d2h = e2e_channel(case, precision, e2e_steps, stream)
+        if pg:
+            t = torch.tensor([e_ms], device="cuda")
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            e_ms = float(t.item())
+        e2e = {"value": total_cells * e2e_steps / (e_ms * 1e-3) / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": h2d / e2e_steps, "d2h_bytes_per_step": d2h / e2e_steps,
+               "steps": e2e_steps,
+               "what": "C-ABI with host buffers: pinned FP64 initial field uploaded, steps with "
+                       "plane statistics every 10 steps, moments and statistics read back"}
+
+    variants = {}
+    if not args.no_variants and rank == 0:
+        for name, wl, prec, steps in (("c3_fp32", "c3", lbm.FP32, 2000), ("c3_fp16", "c3", lbm.FP16_SHIFTED, 2000),
+                                      ("c4_fp32", "c4", lbm.FP32, 300), ("c4_fp16", "c4", lbm.FP16_SHIFTED, 300)):
+            c = workload.CASES[wl]
+            vms, vfin = time_channel(c, prec, steps, 20, stream)
+            kms = vms / steps
+            gbs = BYTES_PER_LUP[prec] * c.cells / (kms * 1e-3) / 1e9
+            variants[name] = {"workload": c.name, "cells": c.cells, "MLUPS": c.cells * steps / (vms * 1e-3) / 1e6,
+                              "ms_per_step": kms, "GBs": gbs, "frac": gbs / peak, "finite": vfin}
+
+    if rank != 0:
+        return 0
+    line = {
+        "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": kernel_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if precision == lbm.FP32 else "f32 (fp16 storage)",
+        "data": "synthetic",
+        "config": {"workload": case.name, "grid": [case.nx, case.ny, case.nz], "cells": case.cells,
+                   "re_tau": case.re_tau, "tau0": case.tau, "C_s": case.cs, "wall": "wfb",
+                   "storage": args.precision, "layout": "two-lattice pull",
+                   "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (129 MB): two %.0f MB lattices per step" % (
+                       BYTES_PER_LUP[precision] / 2 * case.cells / 1e6)},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": NCU_TRAFFIC.get((args.workload, args.precision)),
+                     "peak_source": peak_src, "kernel": "k_step", "bytes_per_lup": BYTES_PER_LUP[precision]},
+        "per_gpu_MLUPS": per_gpu_mlups, "finite": finite,
+        "gpu_launches": args.steps,
+        "clocks": clocks.summary(),
+    }
+    if e2e:
+        line["e2e"] = e2e
+    if variants:
+        line["variants"] = variants
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(case)
+        line["cpu_baseline"]["cpu"] = cpu_model()
+    print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,176 @@
+/*
+ * lbm.h - C ABI of the GB300 (sm_103a) LBM-LES channel solver with the
+ * wall-function bounce (WFB) boundary of Han, Ooka & Kikumoto,
+ * "A wall function approach in lattice Boltzmann method: algorithm and
+ * validation using turbulent channel flow" (arXiv 2009.04352).
+ *
+ * One call of lbm_step advances the lattice Boltzmann equation (Eq. 1) by one
+ * time step per iteration: a single fused CUDA kernel gathers the 19 D3Q19
+ * populations of every cell (streaming, Eq. 1 left side), forms the moments
+ * (Eq. 2), relaxes them with BGK plus a standard Smagorinsky eddy viscosity
+ * (Sec. 3.1) and the Guo body force F_a (Eq. 1 right side), and at the two wall
+ * layers applies bounce-back or the WFB reassignment (Eqs. 14-15) with the wall
+ * stress from Spalding's law (Eqs. 16-17) solved by Newton's method (Sec. 2.3).
+ *
+ * Conventions shared by every entry point:
+ *  - Lattice units: dx = dt = 1, c_s^2 = 1/3, reference density 1.
+ *  - Grid nx * ny * nz: x streamwise and periodic, y wall-normal, z spanwise
+ *    and periodic (the channel of Sec. 3.1, Fig. 3). All ny layers are fluid;
+ *    the walls lie half a link outside them (y = -1/2 and y = ny - 1/2).
+ *  - D3Q19 velocities are numbered as in Table A-1 (Appendix A).
+ *  - Dense cell arrays are [nz][ny][nx] with x fastest; population arrays are
+ *    [19][nz][ny][nx]; wall arrays are [2 walls: bottom, top][nz][nx][2: x, z].
+ *  - Every call is ordered on the handle's CUDA stream. Calls that write to
+ *    host memory synchronise that stream before returning; calls that write to
+ *    device memory do not.
+ *  - Return value: LBM_OK (0) or a negative LBM_ERR_* code. Nothing throws
+ *    across the ABI. lbm_last_error() returns a message for the most recent
+ *    failure on the calling thread.
+ *  - Ownership: the library owns every device buffer it allocates and frees
+ *    them in lbm_destroy. Pointers passed in stay owned by the caller and are
+ *    not retained after the call returns.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_Q 19
+#define LBM_K_STATS 11   /* plane statistics per layer, see lbm_plane_stats */
+#define LBM_K_WALL 4     /* wall statistics per wall, see lbm_plane_stats */
+
+enum {
+    LBM_OK = 0,
+    LBM_ERR_ARG = -1,       /* invalid argument; nothing was changed */
+    LBM_ERR_CUDA = -2,      /* a CUDA runtime call failed */
+    LBM_ERR_OOM = -3,       /* device allocation failed */
+    LBM_ERR_DIVERGED = -4,  /* a conservation check found NaN/Inf */
+    LBM_ERR_STATE = -5      /* call not valid in the handle's current state */
+};
+
+typedef struct { int nx, ny, nz; } lbm_grid;
+
+typedef enum {
+    LBM_WALL_BB = 0,        /* halfway bounce-back: the no-slip reference (Sec. 2.1, Eq. 3) */
+    LBM_WALL_WFB = 1,       /* wall-function bounce (Sec. 2.2, Eqs. 14-15) */
+    LBM_WALL_FREESLIP = 2   /* specular reflection (Sec. 2.1, Eq. 4); WFB with tau_w = 0 */
+} lbm_wall_kind;
+
+/* Wall model of the WFB boundary (Sec. 2.3). kappa and B are the constants of
+ * Spalding's law (Eq. 16; the paper uses 0.41 and 5.5). y1 is the wall
+ * distance entering y+ = y1 u_tau / nu (Eq. 17); 1.0 reproduces the first-layer
+ * y+ printed in Table 1. nu is the molecular viscosity used by the wall law;
+ * a value <= 0 selects (tau - 1/2) / 3. newton_iters caps the Newton
+ * iterations per wall cell and step (<= 0 selects 12); iteration stops earlier
+ * once every lane of a warp has a relative step below 1e-7. */
+typedef struct {
+    int kind;            /* lbm_wall_kind */
+    double kappa;
+    double B;
+    double y1;
+    double nu;
+    int newton_iters;
+} lbm_wall_model;
+
+typedef enum {
+    LBM_FP32 = 0,          /* populations stored as FP32 deviations f_a - w_a */
+    LBM_FP16_SHIFTED = 1   /* populations stored as FP16 deviations f_a - w_a */
+} lbm_precision;
+
+typedef enum {
+    LBM_PULL2 = 0          /* two lattices, gather from neighbours, write own cell */
+} lbm_layout;
+
+typedef struct lbm_handle lbm_handle;
+
+/* Create a lattice at rest (f_a = w_a, rho = 1, u = 0).
+ *   g          grid; nx >= 1, ny >= 2, nz >= 1, nx * ny * nz <= 2^31 - 1 cells.
+ *   tau        BGK relaxation time tau0 > 1/2 (molecular viscosity (tau0 - 1/2)/3).
+ *   C_s        Smagorinsky constant (>= 0; 0 turns the LES model off).
+ *   force      body force per unit volume (F_x, F_y, F_z), host pointer.
+ *   wm         wall model of both walls.
+ *   precision  lbm_precision.
+ *   layout     lbm_layout.
+ *   cuda_stream  cudaStream_t to order all work on; NULL selects the legacy
+ *              default stream.
+ *   out        receives the handle.
+ * Allocates 2 * 19 * cells populations plus small wall and statistics buffers
+ * on the current device. Errors: LBM_ERR_ARG, LBM_ERR_OOM, LBM_ERR_CUDA. */
+int lbm_create(lbm_grid g, double tau, double C_s, const double force[3],
+               lbm_wall_model wm, int precision, int layout, void *cuda_stream,
+               lbm_handle **out);
+
+/* Seeded channel initial field: f = f^eq(rho = 1, u0) (second-order D3Q19
+ * equilibrium) with u0_x = u_mean_x[y] + a (2 U_0 - 1), u0_y = a (2 U_1 - 1),
+ * u0_z = a (2 U_2 - 1), a = noise_amp, and U_c the uniform [0,1) variate
+ * (top 53 bits x 2^-53) of the first SplitMix64 output for state
+ * seed XOR (3 * cell + c), cell = (z * ny + y) * nx + x.
+ *   u_mean_x  host array [ny]. Resets the step counter to 0. */
+int lbm_init_channel(lbm_handle *h, const double *u_mean_x, double noise_amp, uint64_t seed);
+
+/* Replace the populations by host_in (FP64, [19][nz][ny][nx], not shifted).
+ * Rounded once to the storage precision. Resets the step counter to 0. */
+int lbm_set_populations(lbm_handle *h, const double *host_in);
+
+/* Copy the current populations f_a(x, t) to host_out (FP64, [19][nz][ny][nx],
+ * not shifted). Synchronises the stream. */
+int lbm_populations(lbm_handle *h, double *host_out);
+
+/* Sample plane statistics at every step whose index t (before the step) is a
+ * multiple of `every` (0 = never). Sampling is fused into that step's kernel. */
+int lbm_set_stats_every(lbm_handle *h, int every);
+
+/* Advance n >= 0 time steps (Eq. 1 with the wall treatment of Eqs. 14-17).
+ * Asynchronous on the handle's stream; steps without sampling are replayed
+ * from CUDA graphs. */
+int lbm_step(lbm_handle *h, int n);
+
+/* Number of steps taken since the last (re)initialisation. */
+long long lbm_get_step(lbm_handle *h);
+
+/* Density rho [nz][ny][nx] and velocity u [3][nz][ny][nx] of the current
+ * populations (Eq. 2 with the Guo half-force shift, u = (sum e f + F/2)/rho),
+ * FP32. on_device != 0: rho and u are device pointers and the call is
+ * asynchronous; otherwise host pointers and the stream is synchronised.
+ * Either pointer may be NULL. */
+int lbm_moments(lbm_handle *h, float *rho, float *u, int on_device);
+
+/* Wall stress of the most recent step, [2][nz][nx][2] FP32: the tangential
+ * momentum (x, z) the wall treatment added to each wall cell in that step.
+ * For WFB this is (tau_w,x, tau_w,z) of Eq. 15 (dt = dy = 1); for bounce-back
+ * the momentum exchanged by the reflection; zero for free-slip. */
+int lbm_wall_stress(lbm_handle *h, float *tau, int on_device);
+
+/* Accumulated plane statistics (FP64), summed over the cells of each layer and
+ * over the sampled steps (time and plane averaging of Sec. 3.1):
+ *   out [ny][LBM_K_STATS] = rho, u_x, u_y, u_z, u_x^2, u_y^2, u_z^2, u_x u_y,
+ *                           rho u_x, rho u_y, rho u_z  (u as in lbm_moments)
+ *   wall_out [2][LBM_K_WALL] = sum of tau_w,x, tau_w,z, |tau_w|, |tau_w|^2
+ *   n_samples = number of sampled steps.
+ * Host pointers (each may be NULL); synchronises. reset != 0 clears the sums. */
+int lbm_plane_stats(lbm_handle *h, double *out, double *wall_out, long long *n_samples,
+                    int reset);
+
+/* Global mass and raw momentum of the current populations, out[4] =
+ * (sum f, sum e_x f, sum e_y f, sum e_z f), reduced in FP64 (host pointer;
+ * synchronises). Returns LBM_ERR_DIVERGED if any sum is NaN or Inf. */
+int lbm_conservation(lbm_handle *h, double *out);
+
+/* Block until all work queued on the handle's stream has finished. */
+int lbm_sync(lbm_handle *h);
+
+/* Free every device resource of the handle. NULL is ignored. */
+void lbm_destroy(lbm_handle *h);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *lbm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

@@ -1,0 +1,413 @@
+// C ABI of the single-channel solver (declared in include/lbm.h): handle
+// management, step orchestration with CUDA graphs, statistics and exports.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "lbm.h"
+#include "lbm_kernels.cuh"
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define CK(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) return fail(LBM_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+#define CK_LAUNCH() CK(cudaGetLastError())
+
+constexpr int kGraphSteps = 16;   // steps captured per chunk graph (even)
+
+}  // namespace
+
+struct lbm_handle {
+    lbm::Geom g;
+    lbm::Phys p;
+    int precision;
+    int layout;
+    cudaStream_t stream;
+    cudaStream_t cap;            // private stream used only for graph capture
+    void *f[2];                  // two lattices
+    int cur;                     // lattice holding the current post-collision state
+    long long step;
+    int stats_every;
+    float *tw;                   // [2][nz][nx][2]
+    double *part;                // block partials
+    long long part_len;          // doubles
+    double *acc;                 // [ny][K_STATS] then [2][K_WALL]
+    long long nsamples;
+    int bx;                      // threads per block along x
+    cudaGraphExec_t chunk[2];    // kGraphSteps plain steps starting from cur = 0 / 1
+};
+
+namespace {
+
+size_t elem_size(const lbm_handle *h) { return h->precision == LBM_FP16_SHIFTED ? 2 : 4; }
+
+dim3 grid_of(const lbm_handle *h, int bx) { return dim3((h->g.nx + bx - 1) / bx, h->g.ny, h->g.nz); }
+
+int launch_step(lbm_handle *h, cudaStream_t s, int src, bool stats)
+{
+    const dim3 grid = grid_of(h, h->bx), block(h->bx);
+    const void *a = h->f[src];
+    void *b = h->f[src ^ 1];
+    if (h->precision == LBM_FP16_SHIFTED) {
+        if (stats)
+            lbm::k_step<__half, true><<<grid, block, 0, s>>>((const __half *)a, (__half *)b, h->g, h->p, h->tw, h->part);
+        else
+            lbm::k_step<__half, false><<<grid, block, 0, s>>>((const __half *)a, (__half *)b, h->g, h->p, h->tw, h->part);
+    } else {
+        if (stats)
+            lbm::k_step<float, true><<<grid, block, 0, s>>>((const float *)a, (float *)b, h->g, h->p, h->tw, h->part);
+        else
+            lbm::k_step<float, false><<<grid, block, 0, s>>>((const float *)a, (float *)b, h->g, h->p, h->tw, h->part);
+    }
+    CK_LAUNCH();
+    if (stats) {
+        const long long per_plane = (long long)grid.x * h->g.nz;
+        lbm::k_reduce_planes<<<h->g.ny, 256, 0, s>>>(h->part, per_plane, h->g.ny, h->acc,
+                                                     h->acc + (long long)h->g.ny * lbm::K_STATS);
+        CK_LAUNCH();
+    }
+    return LBM_OK;
+}
+
+int build_chunk(lbm_handle *h, int start)
+{
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+    int rc = LBM_OK;
+    for (int i = 0; i < kGraphSteps && rc == LBM_OK; ++i) rc = launch_step(h, h->cap, start ^ (i & 1), false);
+    cudaError_t e = cudaStreamEndCapture(h->cap, &graph);
+    if (rc != LBM_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&h->chunk[start], graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    return LBM_OK;
+}
+
+int ensure_part(lbm_handle *h, long long len)
+{
+    if (len <= h->part_len) return LBM_OK;
+    if (h->part) {
+        CK(cudaStreamSynchronize(h->stream));
+        CK(cudaFree(h->part));
+    }
+    h->part = nullptr;
+    h->part_len = 0;
+    if (cudaMalloc((void **)&h->part, len * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LBM_ERR_OOM, "cannot allocate %lld partial sums", len);
+    }
+    h->part_len = len;
+    // the partial buffer is captured by address in the chunk graphs
+    for (int i = 0; i < 2; ++i)
+        if (h->chunk[i]) {
+            cudaGraphExecDestroy(h->chunk[i]);
+            h->chunk[i] = nullptr;
+        }
+    return LBM_OK;
+}
+
+int export_state(lbm_handle *h, float *rho, float *u, double *pops, double *part)
+{
+    const int bx = 128;
+    const dim3 grid = grid_of(h, bx);
+    if (h->precision == LBM_FP16_SHIFTED)
+        lbm::k_export<__half><<<grid, bx, 0, h->stream>>>((const __half *)h->f[h->cur], h->g, h->p, rho, u, pops, part);
+    else
+        lbm::k_export<float><<<grid, bx, 0, h->stream>>>((const float *)h->f[h->cur], h->g, h->p, rho, u, pops, part);
+    CK_LAUNCH();
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *lbm_last_error(void) { return g_err; }
+
+int lbm_create(lbm_grid g, double tau, double C_s, const double force[3], lbm_wall_model wm, int precision,
+               int layout, void *cuda_stream, lbm_handle **out)
+{
+    if (!out) return fail(LBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (g.nx < 1 || g.ny < 2 || g.nz < 1) return fail(LBM_ERR_ARG, "grid needs nx >= 1, ny >= 2, nz >= 1");
+    if (!(tau > 0.5)) return fail(LBM_ERR_ARG, "tau must exceed 1/2");
+    if (!(C_s >= 0.0)) return fail(LBM_ERR_ARG, "C_s must be >= 0");
+    if (!force) return fail(LBM_ERR_ARG, "force is NULL");
+    if (wm.kind < LBM_WALL_BB || wm.kind > LBM_WALL_FREESLIP) return fail(LBM_ERR_ARG, "unknown wall kind");
+    if (wm.kind == LBM_WALL_WFB && !(wm.kappa > 0.0 && wm.y1 > 0.0))
+        return fail(LBM_ERR_ARG, "WFB needs kappa > 0 and y1 > 0");
+    if (precision != LBM_FP32 && precision != LBM_FP16_SHIFTED) return fail(LBM_ERR_ARG, "unknown precision");
+    if (layout != LBM_PULL2) return fail(LBM_ERR_ARG, "unknown layout");
+    const int sx = (g.nx + 31) / 32 * 32;
+    const long long plane = (long long)sx * g.ny * g.nz;
+    if (plane > 2147483647LL) return fail(LBM_ERR_ARG, "grid too large (row-padded cells > 2^31 - 1)");
+
+    lbm_handle *h = new lbm_handle();
+    memset(h, 0, sizeof(*h));
+    h->g.nx = g.nx;
+    h->g.ny = g.ny;
+    h->g.nz = g.nz;
+    h->g.sx = sx;
+    h->g.plane = plane;
+    const double nu = wm.nu > 0.0 ? wm.nu : (tau - 0.5) / 3.0;
+    h->p.tau0 = (float)tau;
+    h->p.smag = (float)(18.0 * sqrt(2.0) * C_s * C_s);
+    h->p.Fx = (float)force[0];
+    h->p.Fy = (float)force[1];
+    h->p.Fz = (float)force[2];
+    h->p.wall = wm.kind;
+    h->p.kappa = (float)wm.kappa;
+    h->p.B = (float)wm.B;
+    h->p.ekb = (float)exp(-wm.kappa * wm.B);
+    h->p.y1_over_nu = (float)(wm.y1 / nu);
+    h->p.newton_iters = wm.newton_iters > 0 ? wm.newton_iters : 12;
+    h->precision = precision;
+    h->layout = layout;
+    h->stream = (cudaStream_t)cuda_stream;
+    h->bx = g.nx >= 128 ? 128 : (g.nx >= 64 ? 64 : 32);
+
+    auto bail = [&](int rc) {
+        lbm_destroy(h);
+        return rc;
+    };
+    if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(fail(LBM_ERR_CUDA, "cannot create capture stream"));
+    const size_t bytes = (size_t)lbm::Q * plane * elem_size(h);
+    for (int i = 0; i < 2; ++i) {
+        if (cudaMalloc(&h->f[i], bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return bail(fail(LBM_ERR_OOM, "cannot allocate %zu bytes of populations", bytes));
+        }
+        if (cudaMemsetAsync(h->f[i], 0, bytes, h->stream) != cudaSuccess)
+            return bail(fail(LBM_ERR_CUDA, "memset failed"));
+    }
+    const size_t twb = (size_t)4 * g.nx * g.nz * sizeof(float);
+    const size_t accb = ((size_t)g.ny * lbm::K_STATS + 2 * lbm::K_WALL) * sizeof(double);
+    if (cudaMalloc((void **)&h->tw, twb) != cudaSuccess || cudaMalloc((void **)&h->acc, accb) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(LBM_ERR_OOM, "cannot allocate wall/statistics buffers"));
+    }
+    if (cudaMemsetAsync(h->tw, 0, twb, h->stream) != cudaSuccess ||
+        cudaMemsetAsync(h->acc, 0, accb, h->stream) != cudaSuccess)
+        return bail(fail(LBM_ERR_CUDA, "memset failed"));
+    const long long nblk = (long long)grid_of(h, h->bx).x * g.ny * g.nz;
+    const int rc = ensure_part(h, nblk * lbm::K_PART);
+    if (rc != LBM_OK) return bail(rc);
+    *out = h;
+    return LBM_OK;
+}
+
+int lbm_init_channel(lbm_handle *h, const double *u_mean_x, double noise_amp, uint64_t seed)
+{
+    if (!h || !u_mean_x) return fail(LBM_ERR_ARG, "NULL argument");
+    double *um = nullptr;
+    const size_t b = (size_t)h->g.ny * sizeof(double);
+    if (cudaMallocAsync((void **)&um, b, h->stream) != cudaSuccess) return fail(LBM_ERR_OOM, "profile buffer");
+    CK(cudaMemcpyAsync(um, u_mean_x, b, cudaMemcpyHostToDevice, h->stream));
+    const dim3 grid = grid_of(h, 128);
+    if (h->precision == LBM_FP16_SHIFTED)
+        lbm::k_init_channel<__half><<<grid, 128, 0, h->stream>>>((__half *)h->f[h->cur], h->g, h->p.wall, um, noise_amp,
+                                                                  seed);
+    else
+        lbm::k_init_channel<float><<<grid, 128, 0, h->stream>>>((float *)h->f[h->cur], h->g, h->p.wall, um, noise_amp,
+                                                                 seed);
+    CK_LAUNCH();
+    CK(cudaFreeAsync(um, h->stream));
+    // the host profile must stay valid until the copy has run
+    CK(cudaStreamSynchronize(h->stream));
+    h->step = 0;
+    return LBM_OK;
+}
+
+int lbm_set_populations(lbm_handle *h, const double *host_in)
+{
+    if (!h || !host_in) return fail(LBM_ERR_ARG, "NULL argument");
+    const size_t b = (size_t)lbm::Q * h->g.nx * h->g.ny * h->g.nz * sizeof(double);
+    double *d = nullptr;
+    if (cudaMallocAsync((void **)&d, b, h->stream) != cudaSuccess) return fail(LBM_ERR_OOM, "staging buffer");
+    CK(cudaMemcpyAsync(d, host_in, b, cudaMemcpyHostToDevice, h->stream));
+    const dim3 grid = grid_of(h, 128);
+    if (h->precision == LBM_FP16_SHIFTED)
+        lbm::k_scatter<__half><<<grid, 128, 0, h->stream>>>(d, (__half *)h->f[h->cur], h->g, h->p.wall);
+    else
+        lbm::k_scatter<float><<<grid, 128, 0, h->stream>>>(d, (float *)h->f[h->cur], h->g, h->p.wall);
+    CK_LAUNCH();
+    CK(cudaFreeAsync(d, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->step = 0;
+    return LBM_OK;
+}
+
+int lbm_populations(lbm_handle *h, double *host_out)
+{
+    if (!h || !host_out) return fail(LBM_ERR_ARG, "NULL argument");
+    const size_t b = (size_t)lbm::Q * h->g.nx * h->g.ny * h->g.nz * sizeof(double);
+    double *d = nullptr;
+    if (cudaMallocAsync((void **)&d, b, h->stream) != cudaSuccess) return fail(LBM_ERR_OOM, "staging buffer");
+    int rc = export_state(h, nullptr, nullptr, d, nullptr);
+    if (rc != LBM_OK) return rc;
+    CK(cudaMemcpyAsync(host_out, d, b, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaFreeAsync(d, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+int lbm_set_stats_every(lbm_handle *h, int every)
+{
+    if (!h || every < 0) return fail(LBM_ERR_ARG, "invalid argument");
+    h->stats_every = every;
+    return LBM_OK;
+}
+
+int lbm_step(lbm_handle *h, int n)
+{
+    if (!h || n < 0) return fail(LBM_ERR_ARG, "invalid argument");
+    while (n > 0) {
+        const bool sample = h->stats_every > 0 && (h->step % h->stats_every) == 0;
+        if (sample) {
+            int rc = launch_step(h, h->stream, h->cur, true);
+            if (rc != LBM_OK) return rc;
+            h->nsamples += 1;
+            h->cur ^= 1;
+            h->step += 1;
+            n -= 1;
+            continue;
+        }
+        long long run = n;
+        if (h->stats_every > 0) {
+            const long long to_next = h->stats_every - (h->step % h->stats_every);
+            if (to_next < run) run = to_next;
+        }
+        while (run >= kGraphSteps) {
+            if (!h->chunk[h->cur]) {
+                int rc = build_chunk(h, h->cur);
+                if (rc != LBM_OK) return rc;
+            }
+            CK(cudaGraphLaunch(h->chunk[h->cur], h->stream));
+            h->step += kGraphSteps;
+            run -= kGraphSteps;
+            n -= kGraphSteps;
+        }
+        while (run > 0) {
+            int rc = launch_step(h, h->stream, h->cur, false);
+            if (rc != LBM_OK) return rc;
+            h->cur ^= 1;
+            h->step += 1;
+            run -= 1;
+            n -= 1;
+        }
+    }
+    return LBM_OK;
+}
+
+long long lbm_get_step(lbm_handle *h) { return h ? h->step : -1; }
+
+int lbm_moments(lbm_handle *h, float *rho, float *u, int on_device)
+{
+    if (!h) return fail(LBM_ERR_ARG, "NULL handle");
+    if (!rho && !u) return LBM_OK;
+    if (on_device) return export_state(h, rho, u, nullptr, nullptr);
+    const long long n = (long long)h->g.nx * h->g.ny * h->g.nz;
+    float *d = nullptr;
+    if (cudaMallocAsync((void **)&d, (size_t)4 * n * sizeof(float), h->stream) != cudaSuccess)
+        return fail(LBM_ERR_OOM, "staging buffer");
+    int rc = export_state(h, d, d + n, nullptr, nullptr);
+    if (rc != LBM_OK) return rc;
+    if (rho) CK(cudaMemcpyAsync(rho, d, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    if (u) CK(cudaMemcpyAsync(u, d + n, (size_t)3 * n * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaFreeAsync(d, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+int lbm_wall_stress(lbm_handle *h, float *tau, int on_device)
+{
+    if (!h || !tau) return fail(LBM_ERR_ARG, "NULL argument");
+    const size_t b = (size_t)4 * h->g.nx * h->g.nz * sizeof(float);
+    CK(cudaMemcpyAsync(tau, h->tw, b, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+    if (!on_device) CK(cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+int lbm_plane_stats(lbm_handle *h, double *out, double *wall_out, long long *n_samples, int reset)
+{
+    if (!h) return fail(LBM_ERR_ARG, "NULL handle");
+    const size_t b = (size_t)h->g.ny * lbm::K_STATS * sizeof(double);
+    if (out) CK(cudaMemcpyAsync(out, h->acc, b, cudaMemcpyDeviceToHost, h->stream));
+    if (wall_out)
+        CK(cudaMemcpyAsync(wall_out, h->acc + (size_t)h->g.ny * lbm::K_STATS, 2 * lbm::K_WALL * sizeof(double),
+                           cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (n_samples) *n_samples = h->nsamples;
+    if (reset) {
+        CK(cudaMemsetAsync(h->acc, 0, b + 2 * lbm::K_WALL * sizeof(double), h->stream));
+        h->nsamples = 0;
+    }
+    return LBM_OK;
+}
+
+int lbm_conservation(lbm_handle *h, double *out)
+{
+    if (!h || !out) return fail(LBM_ERR_ARG, "NULL argument");
+    const dim3 grid = grid_of(h, 128);
+    const long long nblk = (long long)grid.x * grid.y * grid.z;
+    double *d = nullptr;
+    if (cudaMallocAsync((void **)&d, (size_t)(nblk * 4 + 4) * sizeof(double), h->stream) != cudaSuccess)
+        return fail(LBM_ERR_OOM, "conservation buffer");
+    int rc = export_state(h, nullptr, nullptr, nullptr, d);
+    if (rc != LBM_OK) return rc;
+    lbm::k_reduce_all<<<1, 256, 0, h->stream>>>(d, nblk, d + nblk * 4);
+    CK_LAUNCH();
+    CK(cudaMemcpyAsync(out, d + nblk * 4, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaFreeAsync(d, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    // the partials are deviations from the rest state: add sum w = 1 per cell
+    out[0] += (double)h->g.nx * h->g.ny * h->g.nz;
+    for (int k = 0; k < 4; ++k)
+        if (!isfinite(out[k])) return fail(LBM_ERR_DIVERGED, "non-finite conservation sum (component %d)", k);
+    return LBM_OK;
+}
+
+int lbm_sync(lbm_handle *h)
+{
+    if (!h) return fail(LBM_ERR_ARG, "NULL handle");
+    CK(cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+void lbm_destroy(lbm_handle *h)
+{
+    if (!h) return;
+    if (h->stream || h->f[0]) cudaStreamSynchronize(h->stream);
+    for (int i = 0; i < 2; ++i) {
+        if (h->chunk[i]) cudaGraphExecDestroy(h->chunk[i]);
+        if (h->f[i]) cudaFree(h->f[i]);
+    }
+    if (h->part) cudaFree(h->part);
+    if (h->tw) cudaFree(h->tw);
+    if (h->acc) cudaFree(h->acc);
+    if (h->cap) cudaStreamDestroy(h->cap);
+    delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,189 @@
+// Device-side building blocks of the fused D3Q19 LBM-LES update with the
+// wall-function bounce (WFB) boundary (Han, Ooka & Kikumoto, arXiv 2009.04352).
+//
+// Storage: populations are kept as deviations fb_a = f_a - w_a from the rest
+// state, in FP32 or FP16, structure-of-arrays [19][nz][ny][sx] with x fastest
+// (sx = row pitch >= nx). The two-lattice pull scheme keeps post-collision
+// values: streaming is a gather from the neighbours at the start of the next
+// step. At a wall layer the populations that left toward the wall in the
+// previous step are taken from the specular (WFB, free-slip) or opposite
+// (bounce-back) slot, so the WFB correction of Eq. 14a,b is added when the
+// wall-bound population is stored.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbm {
+
+constexpr int Q = 19;
+
+// D3Q19 velocities, numbered as in Table A-1.
+__host__ __device__ constexpr int ex_of(int a)
+{
+    constexpr int v[Q] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 0, 0, 1, -1, 1, -1, 0, 0};
+    return v[a];
+}
+__host__ __device__ constexpr int ey_of(int a)
+{
+    constexpr int v[Q] = {0, 0, 0, 1, -1, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 1, -1};
+    return v[a];
+}
+__host__ __device__ constexpr int ez_of(int a)
+{
+    constexpr int v[Q] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 1, -1, 1, -1, 0, 0, -1, 1, -1, 1};
+    return v[a];
+}
+// Opposite direction: the pairs (1,2), (3,4), ... of Table A-1.
+__host__ __device__ constexpr int opp_of(int a) { return a == 0 ? 0 : ((a & 1) ? a + 1 : a - 1); }
+// y-mirror (specular partner in a y = const wall): 3<->4, 7<->13, 8<->14,
+// 11<->18, 12<->17, the rest unchanged (Eq. 14a,b partners).
+__host__ __device__ constexpr int mirror_of(int a)
+{
+    constexpr int v[Q] = {0, 1, 2, 4, 3, 5, 6, 13, 14, 9, 10, 18, 17, 7, 8, 15, 16, 12, 11};
+    return v[a];
+}
+// Weights 1/3, 1/18, 1/36 (the DdQq scheme the paper cites as ref. [27]).
+__host__ __device__ constexpr double w_of(int a) { return a == 0 ? 1.0 / 3.0 : (a <= 6 ? 1.0 / 18.0 : 1.0 / 36.0); }
+
+enum { WALL_BB = 0, WALL_WFB = 1, WALL_FREESLIP = 2 };
+enum { ROW_INTERIOR = 0, ROW_BOTTOM = 1, ROW_TOP = 2 };
+
+// Statistics layout of one block partial: 11 plane sums then 4 wall sums.
+constexpr int K_STATS = 11;
+constexpr int K_WALL = 4;
+constexpr int K_PART = K_STATS + K_WALL;
+
+struct Geom {
+    int nx, ny, nz;
+    int sx;              // row pitch in elements
+    long long plane;     // elements per population = sx * ny * nz
+};
+
+struct Phys {
+    float tau0;
+    float smag;          // 18 sqrt(2) C_s^2 (Smagorinsky closure coefficient)
+    float Fx, Fy, Fz;
+    int wall;            // WALL_*
+    float kappa, B;
+    float ekb;           // exp(-kappa B)
+    float y1_over_nu;    // y1 / nu of the wall law
+    int newton_iters;
+};
+
+template <typename T> __device__ __forceinline__ float ld(const T *p);
+template <> __device__ __forceinline__ float ld<float>(const float *p) { return __ldg(p); }
+template <> __device__ __forceinline__ float ld<__half>(const __half *p) { return __half2float(__ldg(p)); }
+
+template <typename T> __device__ __forceinline__ void st(T *p, float v);
+template <> __device__ __forceinline__ void st<float>(float *p, float v) { *p = v; }
+template <> __device__ __forceinline__ void st<__half>(__half *p, float v) { *p = __float2half_rn(v); }
+
+// Element offset that the gather of population a at cell (x, y, z) reads.
+// Periodic wrap in x and z; at the wall layers the population that would come
+// from outside the channel is the one that left toward the wall in the
+// previous step: the own cell's opposite slot (bounce-back) or the mirrored
+// slot of the cell displaced by the tangential part of e_a (specular, WFB).
+template <int ROW>
+__device__ __forceinline__ long long src_offset(const Geom &g, int wall, int a, int x, int y, int z,
+                                                int xm, int xp, int zm, int zp)
+{
+    const int ex = ex_of(a), ey = ey_of(a), ez = ez_of(a);
+    int xs = ex == 1 ? xm : (ex == -1 ? xp : x);
+    int zs = ez == 1 ? zm : (ez == -1 ? zp : z);
+    int ys = y - ey;
+    int slot = a;
+    const bool crosses = (ROW == ROW_BOTTOM && ey == 1) || (ROW == ROW_TOP && ey == -1);
+    if (crosses) {
+        ys = y;
+        if (wall == WALL_BB) {
+            xs = x;
+            zs = z;
+            slot = opp_of(a);
+        } else {
+            slot = mirror_of(a);
+        }
+    }
+    return (long long)slot * g.plane + ((long long)zs * g.ny + ys) * g.sx + xs;
+}
+
+struct Nbr {
+    int xm, xp, zm, zp;
+};
+
+__device__ __forceinline__ Nbr neighbours(const Geom &g, int x, int z)
+{
+    Nbr n;
+    n.xm = x == 0 ? g.nx - 1 : x - 1;
+    n.xp = x == g.nx - 1 ? 0 : x + 1;
+    n.zm = z == 0 ? g.nz - 1 : z - 1;
+    n.zp = z == g.nz - 1 ? 0 : z + 1;
+    return n;
+}
+
+template <typename T, int ROW>
+__device__ __forceinline__ void gather_row(const T *__restrict__ src, const Geom &g, int wall, int x, int y,
+                                           int z, const Nbr &n, float (&fb)[Q])
+{
+#pragma unroll
+    for (int a = 0; a < Q; ++a) fb[a] = ld<T>(src + src_offset<ROW>(g, wall, a, x, y, z, n.xm, n.xp, n.zm, n.zp));
+}
+
+template <typename T>
+__device__ __forceinline__ void gather(const T *__restrict__ src, const Geom &g, int wall, int x, int y, int z,
+                                       float (&fb)[Q])
+{
+    const Nbr n = neighbours(g, x, z);
+    if (y == 0)
+        gather_row<T, ROW_BOTTOM>(src, g, wall, x, y, z, n, fb);
+    else if (y == g.ny - 1)
+        gather_row<T, ROW_TOP>(src, g, wall, x, y, z, n, fb);
+    else
+        gather_row<T, ROW_INTERIOR>(src, g, wall, x, y, z, n, fb);
+}
+
+// Moments of the deviations: drho = sum fb (rho - 1) and j = sum e fb
+// (sum e w = 0, so j is the full momentum).
+struct Moments {
+    float drho, jx, jy, jz;
+};
+
+__device__ __forceinline__ Moments moments_of(const float (&f)[Q])
+{
+    Moments m;
+    m.drho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + ((f[8] + f[9]) + (f[10] + f[11])) +
+             ((f[12] + f[13]) + (f[14] + f[15])) + ((f[16] + f[17]) + f[18]);
+    m.jx = ((f[1] - f[2]) + (f[7] - f[8])) + ((f[9] - f[10]) + (f[13] - f[14])) + (f[15] - f[16]);
+    m.jy = ((f[3] - f[4]) + (f[7] - f[8])) + ((f[11] - f[12]) + (f[14] - f[13])) + (f[17] - f[18]);
+    m.jz = ((f[5] - f[6]) + (f[9] - f[10])) + ((f[11] - f[12]) + (f[16] - f[15])) + (f[18] - f[17]);
+    return m;
+}
+
+// Spalding's law (Eq. 16) inverted for u+ by Newton's method (Sec. 2.3) on
+// h(u+) = u+ y+(u+) - R, R = y1 |u_t| / nu (Eq. 17 gives y+ = R / u+). h is
+// increasing and convex, so any start at or above the root descends
+// monotonically. The start is the laminar guess sqrt(R), lowered for R > 100
+// to the log-law bound ln(R)/kappa + B, which also lies above the root and
+// saves the slow exponential-regime steps. All lanes of the warp iterate
+// together and stop when every lane's relative step is below 1e-7.
+__device__ __forceinline__ float spalding_uplus(float R, const Phys &p, unsigned mask)
+{
+    float up = sqrtf(R);
+    if (R > 100.f) up = fminf(up, logf(R) / p.kappa + p.B);
+    for (int it = 0; it < p.newton_iters; ++it) {
+        const float k = p.kappa * up;
+        const float ek = expf(k);
+        const float t2 = ek - 1.f - k - 0.5f * k * k;        // e^k - 1 - k - k^2/2
+        const float t3 = t2 - k * k * k * (1.f / 6.f);      // ... - k^3/6
+        const float S = up + p.ekb * t3;                     // y+(u+)
+        const float dS = 1.f + p.ekb * p.kappa * t2;         // dy+/du+
+        const float step = (up * S - R) / (S + up * dS);
+        up -= step;
+        const bool done = fabsf(step) <= 1e-7f * up;
+        if (__all_sync(mask, done)) break;
+    }
+    return up;
+}
+
+}  // namespace lbm

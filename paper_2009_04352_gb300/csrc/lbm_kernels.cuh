@@ -1,0 +1,373 @@
+// Kernels of the fused LBM-LES channel step (see lbm_device.cuh for the
+// storage scheme). One thread updates one cell; a block covers a run of x
+// cells of one (y, z) row, so the wall-layer branch is uniform per block.
+#pragma once
+
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+// Post-collision populations of one cell: BGK with the Smagorinsky relaxation
+// time and the Guo forcing (Eq. 1), on deviations from the rest state.
+//   rho = 1 + drho, u = (j + F/2) / rho (Eq. 2 with the Guo half-force shift)
+//   Pi_neq = sum e e (f - f^eq) = sum e e fb - c_s^2 drho I - rho u u
+//   tau_eff = (tau0 + sqrt(tau0^2 + 18 sqrt(2) C_s^2 |Pi_neq| / rho)) / 2
+//   fb*_a = (1 - omega) fb_a + omega (f^eq_a - w_a) + F_a,  omega = 1 / tau_eff
+//   f^eq_a - w_a = w_a [drho + rho (3 e.u + 9/2 (e.u)^2 - 3/2 u.u)]
+//   F_a = (1 - omega / 2) w_a [3 (e_a - u) . F + 9 (e_a . u)(e_a . F)]
+// Opposite directions share the even part and negate the odd part.
+struct CellState {
+    float rho, ux, uy, uz;
+};
+
+__device__ __forceinline__ CellState collide(const float (&f)[Q], float (&fs)[Q], const Phys &p)
+{
+    const Moments m = moments_of(f);
+    CellState c;
+    c.rho = 1.f + m.drho;
+    const float irho = 1.f / c.rho;
+    c.ux = (m.jx + 0.5f * p.Fx) * irho;
+    c.uy = (m.jy + 0.5f * p.Fy) * irho;
+    c.uz = (m.jz + 0.5f * p.Fz) * irho;
+    const float ux = c.ux, uy = c.uy, uz = c.uz, rho = c.rho;
+
+    // second moments of the deviations
+    float pxx = ((f[1] + f[2]) + (f[7] + f[8])) + ((f[9] + f[10]) + (f[13] + f[14])) + (f[15] + f[16]);
+    float pyy = ((f[3] + f[4]) + (f[7] + f[8])) + ((f[11] + f[12]) + (f[13] + f[14])) + (f[17] + f[18]);
+    float pzz = ((f[5] + f[6]) + (f[9] + f[10])) + ((f[11] + f[12]) + (f[15] + f[16])) + (f[17] + f[18]);
+    float pxy = (f[7] + f[8]) - (f[13] + f[14]);
+    float pxz = (f[9] + f[10]) - (f[15] + f[16]);
+    float pyz = (f[11] + f[12]) - (f[17] + f[18]);
+    const float cd = m.drho * (1.f / 3.f);
+    pxx -= cd + rho * ux * ux;
+    pyy -= cd + rho * uy * uy;
+    pzz -= cd + rho * uz * uz;
+    pxy -= rho * ux * uy;
+    pxz -= rho * ux * uz;
+    pyz -= rho * uy * uz;
+    const float q2 = (pxx * pxx + pyy * pyy + pzz * pzz) + 2.f * (pxy * pxy + pxz * pxz + pyz * pyz);
+    // positive root of tau^2 - tau0 tau - smag Q / (4 rho) = 0, written as
+    // tau0 + (root - tau0) so that a small eddy viscosity is not lost to
+    // cancellation against tau0
+    const float cq = p.smag * sqrtf(q2) * irho;
+    const float tau = p.tau0 + cq / (2.f * (sqrtf(p.tau0 * p.tau0 + cq) + p.tau0));
+    const float omega = 1.f / tau;
+    const float om1 = 1.f - omega;
+    const float gk = 1.f - 0.5f * omega;
+
+    const float usq = ux * ux + uy * uy + uz * uz;
+    const float uF = ux * p.Fx + uy * p.Fy + uz * p.Fz;
+    const float A = omega * (m.drho - 1.5f * rho * usq) - 3.f * gk * uF;  // isotropic part
+    const float Bq = 4.5f * omega * rho;                                   // x (e.u)^2
+    const float Cq = 9.f * gk;                                             // x (e.u)(e.F)
+    const float Dq = 3.f * omega * rho;                                    // x e.u
+    const float Eq = 3.f * gk;                                             // x e.F
+
+    fs[0] = om1 * f[0] + (1.f / 3.f) * A;
+#pragma unroll
+    for (int a = 1; a < Q; a += 2) {
+        const float w = (float)w_of(a);
+        const float eu = ex_of(a) * ux + ey_of(a) * uy + ez_of(a) * uz;
+        const float eF = ex_of(a) * p.Fx + ey_of(a) * p.Fy + ez_of(a) * p.Fz;
+        const float even = w * (A + eu * (Bq * eu + Cq * eF));
+        const float odd = w * (Dq * eu + Eq * eF);
+        fs[a] = om1 * f[a] + even + odd;
+        fs[a + 1] = om1 * f[a + 1] + even - odd;
+    }
+    return c;
+}
+
+// Wall layer after collision: the wall stress and, for WFB, the Eq. 14a,b
+// correction folded into the wall-bound slots. A population b leaving toward
+// the wall returns through the specular partner of b, displaced by b's
+// tangential velocity, and must carry +(1/2) tau_w . e_b (dt = dy = 1): at the
+// bottom wall 13 -> 7 (+x), 8 -> 14 (-x), 18 -> 11 (+z), 12 -> 17 (-z); at the
+// top wall 7 -> 13, 14 -> 8, 11 -> 18, 17 -> 12. The stress itself is
+// tau_w = rho u_tau^2 with u_tau = |u_t| / u+ from Spalding's law, directed
+// against the tangential velocity (Eq. 15). For bounce-back the reported stress
+// is the tangential momentum the reflection returns, -2 sum e_b,t f*_b.
+__device__ __forceinline__ void wall_layer(float (&fs)[Q], const CellState &c, const Phys &p, bool bottom,
+                                           unsigned lanes, float &twx, float &twz)
+{
+    twx = 0.f;
+    twz = 0.f;
+    if (p.wall == WALL_WFB) {
+        const float ut = sqrtf(c.ux * c.ux + c.uz * c.uz);
+        const float R = fmaxf(p.y1_over_nu * ut, 1e-30f);
+        const float up = spalding_uplus(R, p, lanes);
+        const float utau = ut / up;
+        const float tw = c.rho * utau * utau;
+        if (ut > 0.f) {
+            twx = -c.ux / ut * tw;
+            twz = -c.uz / ut * tw;
+        }
+        const float hx = 0.5f * twx, hz = 0.5f * twz;
+        if (bottom) {
+            fs[13] += hx;
+            fs[8] -= hx;
+            fs[18] += hz;
+            fs[12] -= hz;
+        } else {
+            fs[7] += hx;
+            fs[14] -= hx;
+            fs[11] += hz;
+            fs[17] -= hz;
+        }
+    } else if (p.wall == WALL_BB) {
+        if (bottom) {
+            twx = -2.f * (fs[13] - fs[8]);
+            twz = -2.f * (fs[18] - fs[12]);
+        } else {
+            twx = -2.f * (fs[7] - fs[14]);
+            twz = -2.f * (fs[11] - fs[17]);
+        }
+    }
+}
+
+template <int N>
+__device__ __forceinline__ void block_reduce_store(double (&v)[N], double *__restrict__ out)
+{
+    __shared__ double red[32][N];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < N; ++k) red[warp][k] = v[k];
+    }
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    if (threadIdx.x < N) {
+        double s = 0.0;
+        for (int w = 0; w < nw; ++w) s += red[w][threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+}
+
+// One time step, two lattices: gather from src (streaming + wall reflection),
+// collide, wall treatment, store into the own cell of dst. With STATS the
+// block also writes its FP64 partial plane sums (K_PART values) to part.
+template <typename T, bool STATS>
+__global__ void __launch_bounds__(512) k_step(const T *__restrict__ src, T *__restrict__ dst, Geom g, Phys p,
+                                              float *__restrict__ tw_out, double *__restrict__ part)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const bool valid = x < g.nx;
+    if (!STATS && !valid) return;
+    const int xc = valid ? x : 0;
+
+    float f[Q], fs[Q];
+    gather<T>(src, g, p.wall, xc, y, z, f);
+    const CellState c = collide(f, fs, p);
+
+    float twx = 0.f, twz = 0.f;
+    const bool wall_row = (y == 0) || (y == g.ny - 1);
+    if (wall_row) {
+        // lanes of this warp still running: all of them with STATS (no early
+        // exit), otherwise those with x < nx
+        unsigned lanes = 0xffffffffu;
+        if (!STATS) {
+            const int first = blockIdx.x * blockDim.x + (threadIdx.x & ~31);
+            const int nv = g.nx - first;
+            lanes = nv >= 32 ? 0xffffffffu : ((1u << nv) - 1u);
+        }
+        wall_layer(fs, c, p, y == 0, lanes, twx, twz);
+        if (valid) {
+            float2 *t = reinterpret_cast<float2 *>(tw_out) + ((long long)((y == 0 ? 0 : 1) * g.nz + z) * g.nx + x);
+            *t = make_float2(twx, twz);
+        }
+    }
+    if (valid) {
+        T *d = dst + ((long long)z * g.ny + y) * g.sx + x;
+#pragma unroll
+        for (int a = 0; a < Q; ++a) st<T>(d + a * g.plane, fs[a]);
+    }
+    if (STATS) {
+        double v[K_PART];
+        const double r = c.rho, ux = c.ux, uy = c.uy, uz = c.uz;
+        const double tx = twx, tz = twz, m2 = tx * tx + tz * tz;
+        const double on = valid ? 1.0 : 0.0;
+        v[0] = on * r;
+        v[1] = on * ux;
+        v[2] = on * uy;
+        v[3] = on * uz;
+        v[4] = on * ux * ux;
+        v[5] = on * uy * uy;
+        v[6] = on * uz * uz;
+        v[7] = on * ux * uy;
+        v[8] = on * r * ux;
+        v[9] = on * r * uy;
+        v[10] = on * r * uz;
+        v[11] = on * tx;
+        v[12] = on * tz;
+        v[13] = on * sqrt(m2);
+        v[14] = on * m2;
+        const long long blk = ((long long)y * g.nz + z) * gridDim.x + blockIdx.x;
+        block_reduce_store<K_PART>(v, part + blk * K_PART);
+    }
+}
+
+// Sum the block partials of each plane (one block per plane, fixed order, so
+// the result is deterministic) into the FP64 accumulators.
+__global__ void k_reduce_planes(const double *__restrict__ part, long long per_plane, int ny,
+                                double *__restrict__ acc, double *__restrict__ wacc)
+{
+    const int y = blockIdx.x;
+    double v[K_PART];
+#pragma unroll
+    for (int k = 0; k < K_PART; ++k) v[k] = 0.0;
+    for (long long i = threadIdx.x; i < per_plane; i += blockDim.x) {
+        const double *q = part + ((long long)y * per_plane + i) * K_PART;
+#pragma unroll
+        for (int k = 0; k < K_PART; ++k) v[k] += q[k];
+    }
+    __shared__ double tot[K_PART];
+    block_reduce_store<K_PART>(v, tot);
+    __syncthreads();
+    if (threadIdx.x < K_STATS) acc[y * K_STATS + threadIdx.x] += tot[threadIdx.x];
+    if (threadIdx.x < K_WALL) {
+        if (y == 0) wacc[threadIdx.x] += tot[K_STATS + threadIdx.x];
+        if (y == ny - 1) wacc[K_WALL + threadIdx.x] += tot[K_STATS + threadIdx.x];
+    }
+}
+
+// Exports of the current populations f(t) (gathered exactly as the step does):
+// moments (FP32), unshifted populations (FP64) and FP64 block partials of
+// (sum f - 1, sum e f) for the conservation check.
+template <typename T>
+__global__ void __launch_bounds__(256) k_export(const T *__restrict__ src, Geom g, Phys p, float *__restrict__ rho_out,
+                                                float *__restrict__ u_out, double *__restrict__ pop_out,
+                                                double *__restrict__ part)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const bool valid = x < g.nx;
+    const int xc = valid ? x : 0;
+    float f[Q];
+    gather<T>(src, g, p.wall, xc, y, z, f);
+    const long long n = (long long)g.nx * g.ny * g.nz;
+    const long long cell = ((long long)z * g.ny + y) * g.nx + x;
+    if (valid) {
+        if (rho_out || u_out) {
+            const Moments m = moments_of(f);
+            const float rho = 1.f + m.drho;
+            if (rho_out) rho_out[cell] = rho;
+            if (u_out) {
+                u_out[cell] = (m.jx + 0.5f * p.Fx) / rho;
+                u_out[n + cell] = (m.jy + 0.5f * p.Fy) / rho;
+                u_out[2 * n + cell] = (m.jz + 0.5f * p.Fz) / rho;
+            }
+        }
+        if (pop_out) {
+#pragma unroll
+            for (int a = 0; a < Q; ++a) pop_out[a * n + cell] = (double)f[a] + w_of(a);
+        }
+    }
+    if (part) {
+        double v[4] = {0.0, 0.0, 0.0, 0.0};
+        if (valid) {
+#pragma unroll
+            for (int a = 0; a < Q; ++a) {
+                const double fa = f[a];
+                v[0] += fa;
+                v[1] += ex_of(a) * fa;
+                v[2] += ey_of(a) * fa;
+                v[3] += ez_of(a) * fa;
+            }
+        }
+        const long long blk = ((long long)z * g.ny + y) * gridDim.x + blockIdx.x;
+        block_reduce_store<4>(v, part + blk * 4);
+    }
+}
+
+__global__ void k_reduce_all(const double *__restrict__ part, long long nblk, double *__restrict__ out)
+{
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    for (long long i = threadIdx.x; i < nblk; i += blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] += part[i * 4 + k];
+    }
+    block_reduce_store<4>(v, out);
+}
+
+template <typename T> __device__ __forceinline__ void st_d(T *p, double v);
+template <> __device__ __forceinline__ void st_d<float>(float *p, double v) { *p = __double2float_rn(v); }
+template <> __device__ __forceinline__ void st_d<__half>(__half *p, double v) { *p = __double2half(v); }
+
+// Write f_a(x) (FP64, unshifted, dense) into the slot that the gather of
+// (x, a) reads, so that the next gather returns exactly these populations.
+template <typename T>
+__global__ void k_scatter(const double *__restrict__ in, T *__restrict__ dst, Geom g, int wall)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y, z = blockIdx.z;
+    if (x >= g.nx) return;
+    const Nbr n = neighbours(g, x, z);
+    const long long ncell = (long long)g.nx * g.ny * g.nz;
+    const long long cell = ((long long)z * g.ny + y) * g.nx + x;
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        long long off;
+        if (y == 0)
+            off = src_offset<ROW_BOTTOM>(g, wall, a, x, y, z, n.xm, n.xp, n.zm, n.zp);
+        else if (y == g.ny - 1)
+            off = src_offset<ROW_TOP>(g, wall, a, x, y, z, n.xm, n.xp, n.zm, n.zp);
+        else
+            off = src_offset<ROW_INTERIOR>(g, wall, a, x, y, z, n.xm, n.xp, n.zm, n.zp);
+        st_d<T>(dst + off, in[a * ncell + cell] - w_of(a));
+    }
+}
+
+// SplitMix64 (Steele, Lea & Flood 2014): first output for state s.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t s)
+{
+    uint64_t z = s + 0x9e3779b97f4a7c15ULL;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+// Seeded channel field f = f^eq(1, u0), u0 = mean profile + uniform noise, in
+// FP64 without contraction, then rounded once to the storage precision and
+// written to the slots the next gather reads.
+template <typename T>
+__global__ void k_init_channel(T *__restrict__ dst, Geom g, int wall, const double *__restrict__ umean, double amp,
+                               uint64_t seed)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y, z = blockIdx.z;
+    if (x >= g.nx) return;
+    const unsigned long long cell = ((unsigned long long)z * g.ny + y) * g.nx + x;
+    double u[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const double r = (double)(splitmix64(seed ^ (cell * 3ULL + (unsigned long long)c)) >> 11) *
+                         (1.0 / 9007199254740992.0);
+        const double noise = __dmul_rn(__dsub_rn(__dmul_rn(2.0, r), 1.0), amp);
+        u[c] = __dadd_rn(c == 0 ? umean[y] : 0.0, noise);
+    }
+    const double uu = __dadd_rn(__dadd_rn(__dmul_rn(u[0], u[0]), __dmul_rn(u[1], u[1])), __dmul_rn(u[2], u[2]));
+    const Nbr n = neighbours(g, x, z);
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        const double eu = __dadd_rn(__dadd_rn(__dmul_rn((double)ex_of(a), u[0]), __dmul_rn((double)ey_of(a), u[1])),
+                                    __dmul_rn((double)ez_of(a), u[2]));
+        const double poly = __dsub_rn(__dadd_rn(__dadd_rn(1.0, __dmul_rn(3.0, eu)), __dmul_rn(__dmul_rn(4.5, eu), eu)),
+                                      __dmul_rn(1.5, uu));
+        const double feq = __dmul_rn(__dmul_rn(w_of(a), 1.0), poly);
+        long long off;
+        if (y == 0)
+            off = src_offset<ROW_BOTTOM>(g, wall, a, x, y, z, n.xm, n.xp, n.zm, n.zp);
+        else if (y == g.ny - 1)
+            off = src_offset<ROW_TOP>(g, wall, a, x, y, z, n.xm, n.xp, n.zm, n.zp);
+        else
+            off = src_offset<ROW_INTERIOR>(g, wall, a, x, y, z, n.xm, n.xp, n.zm, n.zp);
+        st_d<T>(dst + off, __dsub_rn(feq, w_of(a)));
+    }
+}
+
+}  // namespace lbm

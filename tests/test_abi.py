@@ -1,0 +1,77 @@
+"""Host-side checks of the C ABI: the library builds, loads without a GPU,
+exports every entry point declared in include/lbm.h, and rejects invalid
+arguments before touching the device."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for hdr in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not hdr.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", hdr)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^[A-Za-z_][\w \*]*?\b(lbm_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def built_lib():
+    from paper_2009_04352_gb300 import build
+    path = build.build()
+    return C.CDLL(path)
+
+
+def test_header_declares_entry_points():
+    names = _declared()
+    for required in ("lbm_create", "lbm_step", "lbm_moments", "lbm_wall_stress", "lbm_plane_stats",
+                     "lbm_populations", "lbm_destroy", "lbm_last_error"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(built_lib):
+    for name in _declared():
+        assert hasattr(built_lib, name), name
+
+
+def test_binding_covers_every_symbol():
+    from paper_2009_04352_gb300 import lbm
+    assert set(_declared()) <= set(lbm.exported_symbols())
+
+
+def test_invalid_arguments_rejected_without_device():
+    from paper_2009_04352_gb300 import lbm
+    bad = [dict(nx=8, ny=1, nz=8, tau=0.6),            # ny < 2
+           dict(nx=0, ny=8, nz=8, tau=0.6),            # empty grid
+           dict(nx=8, ny=8, nz=8, tau=0.5),            # tau must exceed 1/2
+           dict(nx=8, ny=8, nz=8, tau=0.6, cs=-1.0),   # negative C_s
+           dict(nx=8, ny=8, nz=8, tau=0.6, wall=7),    # unknown wall
+           dict(nx=8, ny=8, nz=8, tau=0.6, precision=5),
+           dict(nx=8, ny=8, nz=8, tau=0.6, layout=3),
+           dict(nx=1 << 16, ny=1 << 10, nz=1 << 10, tau=0.6)]  # > 2^31 cells
+    for kw in bad:
+        kw = dict(kw)
+        args = dict(cs=0.1, force=(1e-6, 0, 0), wall=lbm.WALL_WFB, precision=lbm.FP32, layout=lbm.PULL2)
+        args.update(kw)
+        with pytest.raises(lbm.LbmError) as ei:
+            lbm.lbm_create(args.pop("nx"), args.pop("ny"), args.pop("nz"), args.pop("tau"), args.pop("cs"),
+                           args.pop("force"), wall=args["wall"], precision=args["precision"],
+                           layout=args["layout"], stream=0)
+        assert ei.value.code == lbm.LBM_ERR_ARG
+        assert lbm.lib().lbm_last_error().decode()
+
+
+def test_null_handle_calls_fail_cleanly():
+    from paper_2009_04352_gb300 import lbm
+    L = lbm.lib()
+    assert L.lbm_step(None, 1) == lbm.LBM_ERR_ARG
+    assert L.lbm_sync(None) == lbm.LBM_ERR_ARG
+    assert L.lbm_get_step(None) == -1
+    L.lbm_destroy(None)

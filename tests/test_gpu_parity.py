@@ -1,0 +1,225 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs. Relative L_inf bounds: 1e-5 for FP32 storage and 5e-3 for
+FP16-shifted storage, measured as max |gpu - oracle| / max |oracle| over
+cells and components (u; rho - 1; populations minus their weights)."""
+import functools
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2009_04352_gb300 import lbm, workload
+
+pytestmark = pytest.mark.gpu
+
+TOL = {lbm.FP32: 1e-5, lbm.FP16_SHIFTED: 5e-3}
+WALLS = [workload.WALL_BB, workload.WALL_WFB, workload.WALL_FREESLIP]
+_W = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2009_04352_gb300 import build
+    build.build()
+    oracle.build()
+
+
+def rel_linf(got, ref):
+    scale = np.max(np.abs(ref))
+    return float(np.max(np.abs(np.asarray(got, dtype=np.float64) - ref)) / max(scale, 1e-300))
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_run(case, wall, checkpoints, stats_every=0):
+    """Moments, wall stress and populations of the oracle at each checkpoint."""
+    L = oracle.Lattice.from_case(case, stats_every=stats_every, wall=wall)
+    L.init_channel(workload.u_mean_profile(case), workload.noise_amplitude(case), case.seed)
+    out = {}
+    t = 0
+    for c in checkpoints:
+        L.step(c - t)
+        t = c
+        rho, u = L.moments()
+        out[c] = dict(rho=rho, u=u, tw=L.wall_stress(), f=L.populations(), cons=L.conservation(),
+                      stats=L.plane_stats())
+    L.close()
+    return out
+
+
+def gpu_channel(case, wall, precision):
+    ch = lbm.Channel.from_case(case, precision=precision, wall=wall)
+    ch.init_channel(workload.u_mean_profile(case), workload.noise_amplitude(case), case.seed)
+    return ch
+
+
+SMALL = workload.CASES["c1"]                       # 64 x 32 x 32, tau0 0.52
+RAGGED = [SMALL.with_(nx=37, ny=6, nz=5), SMALL.with_(nx=1, ny=8, nz=1),
+          SMALL.with_(nx=33, ny=2, nz=3), SMALL.with_(nx=130, ny=5, nz=2)]
+
+
+@pytest.mark.parametrize("precision", [lbm.FP32, lbm.FP16_SHIFTED])
+def test_init_matches_oracle(precision):
+    case = SMALL
+    ref = oracle_run(case, workload.WALL_WFB, (0,))[0]
+    ch = gpu_channel(case, workload.WALL_WFB, precision)
+    f = ch.populations()
+    dev_ref = ref["f"] - _W[:, None, None, None]
+    # one rounding of the deviation to the storage precision
+    ulp = 2.0 ** -24 if precision == lbm.FP32 else 2.0 ** -11
+    assert np.max(np.abs((f - _W[:, None, None, None]) - dev_ref)) <= ulp * np.max(np.abs(dev_ref)) + 1e-12
+    ch.close()
+
+
+@pytest.mark.parametrize("precision", [lbm.FP32, lbm.FP16_SHIFTED])
+@pytest.mark.parametrize("wall", WALLS)
+def test_parity_100_steps(wall, precision):
+    """64x32x32 channel, tau0 0.52, C_s 0.1, seeded log-law + 10% noise: 100 steps."""
+    case = SMALL
+    checkpoints = (1, 10, 50, 100)
+    ref = oracle_run(case, wall, checkpoints)
+    ch = gpu_channel(case, wall, precision)
+    t = 0
+    worst = {}
+    for c in checkpoints:
+        ch.step(c - t)
+        t = c
+        rho, u = ch.moments()
+        e_u = rel_linf(u, ref[c]["u"])
+        e_r = rel_linf(rho - 1.0, ref[c]["rho"] - 1.0)
+        worst[c] = (e_u, e_r)
+        assert e_u <= TOL[precision], (c, e_u)
+        assert e_r <= TOL[precision], (c, e_r)
+    f = ch.populations()
+    e_f = rel_linf(f - _W[:, None, None, None], ref[100]["f"] - _W[:, None, None, None])
+    assert e_f <= TOL[precision], e_f
+    if wall != workload.WALL_FREESLIP:
+        e_t = rel_linf(ch.wall_stress(), ref[100]["tw"])
+        assert e_t <= 10 * TOL[precision], e_t
+    else:
+        assert np.all(ch.wall_stress() == 0.0)
+    ch.close()
+
+
+@pytest.mark.parametrize("case", RAGGED, ids=lambda c: f"{c.nx}x{c.ny}x{c.nz}")
+@pytest.mark.parametrize("wall", WALLS)
+def test_parity_ragged(case, wall):
+    """Rows shorter than a block, not a multiple of 32, a single column, ny = 2."""
+    checkpoints = (1, 7, 20)
+    ref = oracle_run(case, wall, checkpoints)
+    ch = gpu_channel(case, wall, lbm.FP32)
+    t = 0
+    for c in checkpoints:
+        ch.step(c - t)
+        t = c
+        rho, u = ch.moments()
+        assert rel_linf(u, ref[c]["u"]) <= 1e-5
+        assert rel_linf(rho - 1.0, ref[c]["rho"] - 1.0) <= 1e-5
+    ch.close()
+
+
+@pytest.mark.parametrize("wall", [workload.WALL_BB, workload.WALL_WFB])
+def test_plane_stats_and_conservation(wall):
+    case = SMALL.with_(nx=48, ny=12, nz=10)
+    L = oracle.Lattice.from_case(case, stats_every=3, wall=wall)
+    L.init_channel(workload.u_mean_profile(case), workload.noise_amplitude(case), case.seed)
+    L.step(30)
+    st_o, w_o, n_o = L.plane_stats()
+    cons_o = L.conservation()
+
+    ch = gpu_channel(case, wall, lbm.FP32)
+    ch.set_stats_every(3)
+    ch.step(30)
+    st_g, w_g, n_g = ch.plane_stats()
+    cons_g = ch.conservation()
+    assert n_g == n_o == 10
+    # columns: rho and u moments compared relative to each column's scale
+    for k in range(st_o.shape[1]):
+        ref = st_o[:, k]
+        if k == 0:
+            assert np.max(np.abs(st_g[:, 0] - ref)) <= 1e-6 * np.max(np.abs(ref))
+        else:
+            assert rel_linf(st_g[:, k], ref) <= 1e-4, k
+    assert rel_linf(w_g, w_o) <= 1e-4
+    assert abs(cons_g[0] - cons_o[0]) <= 1e-7 * cons_o[0]
+    assert np.max(np.abs(cons_g[1:] - cons_o[1:])) <= 1e-5 * np.max(np.abs(cons_o[1:]))
+    # reset clears the accumulators
+    ch.plane_stats(reset=True)
+    st2, w2, n2 = ch.plane_stats()
+    assert n2 == 0 and np.all(st2 == 0.0) and np.all(w2 == 0.0)
+    ch.close()
+
+
+def test_graph_replay_matches_single_launches():
+    """Chunked CUDA-graph replay gives bit-identical results to one launch per step."""
+    case = SMALL.with_(nx=40, ny=10, nz=6)
+    a = gpu_channel(case, workload.WALL_WFB, lbm.FP32)
+    b = gpu_channel(case, workload.WALL_WFB, lbm.FP32)
+    a.step(70)
+    for _ in range(70):
+        b.step(1)
+    assert a.step_count == b.step_count == 70
+    assert np.array_equal(a.populations(), b.populations())
+    assert np.array_equal(a.wall_stress(), b.wall_stress())
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("wall", WALLS)
+def test_gpu_momentum_budget(wall):
+    """Per step the x and z momentum change by N F + sum of the wall stresses
+    (Eq. 9 / 12b summed), checked on the GPU alone in FP64 reductions."""
+    case = SMALL.with_(nx=32, ny=8, nz=16, force=(2e-6, 0.0, -1e-6))
+    ch = gpu_channel(case, wall, lbm.FP32)
+    p0 = ch.conservation()
+    for _ in range(5):
+        ch.step(1)
+        p1 = ch.conservation()
+        tw = ch.wall_stress().astype(np.float64)
+        for c, comp in ((1, 0), (3, 1)):
+            expect = case.cells * case.force[c - 1] + tw[..., comp].sum()
+            assert abs((p1[c] - p0[c]) - expect) <= 1e-3 * max(abs(expect), case.cells * 1e-6), (wall, c)
+        assert abs(p1[0] - p0[0]) <= 1e-9 * p0[0]
+        p0 = p1
+    ch.close()
+
+
+def test_moments_on_device():
+    import torch
+    case = SMALL.with_(nx=20, ny=6, nz=4)
+    ch = gpu_channel(case, workload.WALL_WFB, lbm.FP32)
+    ch.step(3)
+    rho_h, u_h = ch.moments()
+    rho_d, u_d = ch.moments(device=True)
+    torch.cuda.synchronize()
+    assert np.array_equal(rho_d.cpu().numpy(), rho_h)
+    assert np.array_equal(u_d.cpu().numpy(), u_h)
+    ch.close()
+
+
+def test_set_populations_round_trip():
+    case = SMALL.with_(nx=24, ny=7, nz=5)
+    ref = oracle_run(case, workload.WALL_WFB, (3,))[3]
+    ch = lbm.Channel.from_case(case)
+    ch.set_populations(ref["f"])
+    f = ch.populations()
+    dev = ref["f"] - _W[:, None, None, None]
+    assert np.max(np.abs(f - ref["f"])) <= 2.0 ** -24 * np.max(np.abs(dev)) + 1e-15
+    ch.close()
+
+
+@pytest.mark.parametrize("precision", [lbm.FP32, lbm.FP16_SHIFTED])
+def test_full_size_bench_grid(precision):
+    """256x64x128 (the benchmark's FP32 channel), launch configuration as benched:
+    three steps compared with the oracle on every cell."""
+    case = workload.CASES["c2"]
+    ref = oracle_run(case, workload.WALL_WFB, (3,))[3]
+    ch = gpu_channel(case, workload.WALL_WFB, precision)
+    ch.step(3)
+    rho, u = ch.moments()
+    assert rel_linf(u, ref["u"]) <= TOL[precision]
+    assert rel_linf(rho - 1.0, ref["rho"] - 1.0) <= TOL[precision]
+    assert rel_linf(ch.wall_stress(), ref["tw"]) <= 10 * TOL[precision]
+    ch.close()
