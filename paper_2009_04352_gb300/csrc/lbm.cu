@@ -184,7 +184,7 @@ int lbm_create(lbm_grid g, double tau, double C_s, const double force[3], lbm_wa
     h->precision = precision;
     h->layout = layout;
     h->stream = (cudaStream_t)cuda_stream;
-    h->bx = g.nx >= 128 ? 128 : (g.nx >= 64 ? 64 : 32);
+    h->bx = g.nx >= 128 ? 128 : (g.nx >= 64 ? 64 : 32);   // <= the kernel's launch bound
 
     auto bail = [&](int rc) {
         lbm_destroy(h);

@@ -8,27 +8,42 @@
 namespace lbm {
 
 // Post-collision populations of one cell: BGK with the Smagorinsky relaxation
-// time and the Guo forcing (Eq. 1), on deviations from the rest state.
+// time and the Guo forcing (Eq. 1), on deviations fb_a = f_a - w_a:
 //   rho = 1 + drho, u = (j + F/2) / rho (Eq. 2 with the Guo half-force shift)
 //   Pi_neq = sum e e (f - f^eq) = sum e e fb - c_s^2 drho I - rho u u
 //   tau_eff = (tau0 + sqrt(tau0^2 + 18 sqrt(2) C_s^2 |Pi_neq| / rho)) / 2
-//   fb*_a = (1 - omega) fb_a + omega (f^eq_a - w_a) + F_a,  omega = 1 / tau_eff
+//   fb*_a = fb_a + omega (f^eq_a - w_a - fb_a) + F_a,  omega = 1 / tau_eff
 //   f^eq_a - w_a = w_a [drho + rho (3 e.u + 9/2 (e.u)^2 - 3/2 u.u)]
 //   F_a = (1 - omega / 2) w_a [3 (e_a - u) . F + 9 (e_a . u)(e_a . F)]
-// Opposite directions share the even part and negate the odd part.
+// The update delta_a = fb*_a - fb_a is formed per opposite pair from its even
+// and odd parts. In exact arithmetic sum delta = 0 and sum e delta = F; in
+// FP32 the rounded weights w_a break the lattice isotropy by ~1e-8, which
+// biases the momentum of every cell by ~1e-8 rho u per step, a sizeable
+// fraction of a body force of 1e-7. The odd parts are therefore corrected on
+// the axis pairs so that sum e delta = F, and the rest population takes
+// -sum of the others, so mass and momentum are exact up to the final store.
 struct CellState {
     float rho, ux, uy, uz;
 };
 
+// u = (j + F/2) / rho evaluated as jF + jF (1/rho - 1) with 1/rho - 1 =
+// -drho / rho, which avoids the systematic rounding of 1/rho near 1.
+__device__ __forceinline__ CellState velocity(const Moments &m, const Phys &p)
+{
+    CellState c;
+    c.rho = 1.f + m.drho;
+    const float idev = -m.drho / c.rho;
+    const float jx = m.jx + 0.5f * p.Fx, jy = m.jy + 0.5f * p.Fy, jz = m.jz + 0.5f * p.Fz;
+    c.ux = fmaf(jx, idev, jx);
+    c.uy = fmaf(jy, idev, jy);
+    c.uz = fmaf(jz, idev, jz);
+    return c;
+}
+
 __device__ __forceinline__ CellState collide(const float (&f)[Q], float (&fs)[Q], const Phys &p)
 {
     const Moments m = moments_of(f);
-    CellState c;
-    c.rho = 1.f + m.drho;
-    const float irho = 1.f / c.rho;
-    c.ux = (m.jx + 0.5f * p.Fx) * irho;
-    c.uy = (m.jy + 0.5f * p.Fy) * irho;
-    c.uz = (m.jz + 0.5f * p.Fz) * irho;
+    const CellState c = velocity(m, p);
     const float ux = c.ux, uy = c.uy, uz = c.uz, rho = c.rho;
 
     // second moments of the deviations
@@ -49,30 +64,44 @@ __device__ __forceinline__ CellState collide(const float (&f)[Q], float (&fs)[Q]
     // positive root of tau^2 - tau0 tau - smag Q / (4 rho) = 0, written as
     // tau0 + (root - tau0) so that a small eddy viscosity is not lost to
     // cancellation against tau0
-    const float cq = p.smag * sqrtf(q2) * irho;
+    const float cq = p.smag * sqrtf(q2) / rho;
     const float tau = p.tau0 + cq / (2.f * (sqrtf(p.tau0 * p.tau0 + cq) + p.tau0));
     const float omega = 1.f / tau;
-    const float om1 = 1.f - omega;
     const float gk = 1.f - 0.5f * omega;
 
     const float usq = ux * ux + uy * uy + uz * uz;
     const float uF = ux * p.Fx + uy * p.Fy + uz * p.Fz;
-    const float A = omega * (m.drho - 1.5f * rho * usq) - 3.f * gk * uF;  // isotropic part
-    const float Bq = 4.5f * omega * rho;                                   // x (e.u)^2
-    const float Cq = 9.f * gk;                                             // x (e.u)(e.F)
-    const float Dq = 3.f * omega * rho;                                    // x e.u
-    const float Eq = 3.f * gk;                                             // x e.F
+    const float S0 = m.drho - 1.5f * rho * usq;   // isotropic part of (f^eq - w) / w
+    const float r45 = 4.5f * rho, r3 = 3.f * rho;
+    const float g9 = 9.f * gk, g3 = 3.f * gk;
 
-    fs[0] = om1 * f[0] + (1.f / 3.f) * A;
+    float de[9], dd[9];
+    float mass = 0.f, mx = 0.f, my = 0.f, mz = 0.f;
 #pragma unroll
-    for (int a = 1; a < Q; a += 2) {
+    for (int k = 0; k < 9; ++k) {
+        const int a = 2 * k + 1;
         const float w = (float)w_of(a);
         const float eu = ex_of(a) * ux + ey_of(a) * uy + ez_of(a) * uz;
         const float eF = ex_of(a) * p.Fx + ey_of(a) * p.Fy + ez_of(a) * p.Fz;
-        const float even = w * (A + eu * (Bq * eu + Cq * eF));
-        const float odd = w * (Dq * eu + Eq * eF);
-        fs[a] = om1 * f[a] + even + odd;
-        fs[a + 1] = om1 * f[a + 1] + even - odd;
+        const float fe = 0.5f * (f[a] + f[a + 1]);
+        const float fo = 0.5f * (f[a] - f[a + 1]);
+        de[k] = omega * (w * (S0 + r45 * eu * eu) - fe) + w * (g9 * eu * eF - g3 * uF);
+        dd[k] = omega * (w * (r3 * eu) - fo) + w * (g3 * eF);
+        mass += de[k];
+        if (ex_of(a)) mx += ex_of(a) * dd[k];
+        if (ey_of(a)) my += ey_of(a) * dd[k];
+        if (ez_of(a)) mz += ez_of(a) * dd[k];
+    }
+    // pairs 0, 1, 2 are the axis directions 1, 3, 5 (e = unit x, y, z)
+    dd[0] += 0.5f * p.Fx - mx;
+    dd[1] += 0.5f * p.Fy - my;
+    dd[2] += 0.5f * p.Fz - mz;
+    fs[0] = f[0] - 2.f * mass;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const int a = 2 * k + 1;
+        fs[a] = f[a] + (de[k] + dd[k]);
+        fs[a + 1] = f[a + 1] + (de[k] - dd[k]);
     }
     return c;
 }
@@ -151,7 +180,7 @@ __device__ __forceinline__ void block_reduce_store(double (&v)[N], double *__res
 // collide, wall treatment, store into the own cell of dst. With STATS the
 // block also writes its FP64 partial plane sums (K_PART values) to part.
 template <typename T, bool STATS>
-__global__ void __launch_bounds__(512) k_step(const T *__restrict__ src, T *__restrict__ dst, Geom g, Phys p,
+__global__ void __launch_bounds__(128) k_step(const T *__restrict__ src, T *__restrict__ dst, Geom g, Phys p,
                                               float *__restrict__ tw_out, double *__restrict__ part)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -253,13 +282,12 @@ __global__ void __launch_bounds__(256) k_export(const T *__restrict__ src, Geom 
     const long long cell = ((long long)z * g.ny + y) * g.nx + x;
     if (valid) {
         if (rho_out || u_out) {
-            const Moments m = moments_of(f);
-            const float rho = 1.f + m.drho;
-            if (rho_out) rho_out[cell] = rho;
+            const CellState c = velocity(moments_of(f), p);
+            if (rho_out) rho_out[cell] = c.rho;
             if (u_out) {
-                u_out[cell] = (m.jx + 0.5f * p.Fx) / rho;
-                u_out[n + cell] = (m.jy + 0.5f * p.Fy) / rho;
-                u_out[2 * n + cell] = (m.jz + 0.5f * p.Fz) / rho;
+                u_out[cell] = c.ux;
+                u_out[n + cell] = c.uy;
+                u_out[2 * n + cell] = c.uz;
             }
         }
         if (pop_out) {
