@@ -6,7 +6,7 @@
 #include <string.h>
 
 #include "lbm.h"
-#include "lbm_kernels.cuh"
+#include "lbm_pair.cuh"
 
 namespace {
 
@@ -50,6 +50,7 @@ struct lbm_handle {
     double *acc;                 // [ny][K_STATS] then [2][K_WALL]
     long long nsamples;
     int bx;                      // threads per block along x
+    bool pair;                   // two cells per thread (even nx)
     cudaGraphExec_t chunk[2];    // kGraphSteps plain steps starting from cur = 0 / 1
 };
 
@@ -59,12 +60,32 @@ size_t elem_size(const lbm_handle *h) { return h->precision == LBM_FP16_SHIFTED 
 
 dim3 grid_of(const lbm_handle *h, int bx) { return dim3((h->g.nx + bx - 1) / bx, h->g.ny, h->g.nz); }
 
+// grid of the step kernel: one thread per cell, or per x-pair for even nx
+dim3 step_grid(const lbm_handle *h)
+{
+    const int per_row = h->pair ? h->g.nx / 2 : h->g.nx;
+    return dim3((per_row + h->bx - 1) / h->bx, h->g.ny, h->g.nz);
+}
+
 int launch_step(lbm_handle *h, cudaStream_t s, int src, bool stats)
 {
-    const dim3 grid = grid_of(h, h->bx), block(h->bx);
+    const dim3 grid = step_grid(h), block(h->bx);
     const void *a = h->f[src];
     void *b = h->f[src ^ 1];
-    if (h->precision == LBM_FP16_SHIFTED) {
+    if (h->pair && h->precision == LBM_FP16_SHIFTED) {
+        if (stats)
+            lbm::k_step_pair<__half, true><<<grid, block, 0, s>>>((const __half *)a, (__half *)b, h->g, h->p, h->tw,
+                                                                  h->part);
+        else
+            lbm::k_step_pair<__half, false><<<grid, block, 0, s>>>((const __half *)a, (__half *)b, h->g, h->p, h->tw,
+                                                                   h->part);
+    } else if (h->pair) {
+        if (stats)
+            lbm::k_step_pair<float, true><<<grid, block, 0, s>>>((const float *)a, (float *)b, h->g, h->p, h->tw, h->part);
+        else
+            lbm::k_step_pair<float, false><<<grid, block, 0, s>>>((const float *)a, (float *)b, h->g, h->p, h->tw,
+                                                                  h->part);
+    } else if (h->precision == LBM_FP16_SHIFTED) {
         if (stats)
             lbm::k_step<__half, true><<<grid, block, 0, s>>>((const __half *)a, (__half *)b, h->g, h->p, h->tw, h->part);
         else
@@ -184,7 +205,12 @@ int lbm_create(lbm_grid g, double tau, double C_s, const double force[3], lbm_wa
     h->precision = precision;
     h->layout = layout;
     h->stream = (cudaStream_t)cuda_stream;
-    h->bx = g.nx >= 128 ? 128 : (g.nx >= 64 ? 64 : 32);   // <= the kernel's launch bound
+    h->pair = (g.nx % 2) == 0;
+    {
+        // threads per block (<= the kernels' launch bound of 128), a multiple of 32
+        const int per_row = h->pair ? g.nx / 2 : g.nx;
+        h->bx = per_row >= 128 ? 128 : (per_row > 32 ? 64 : 32);
+    }
 
     auto bail = [&](int rc) {
         lbm_destroy(h);
@@ -210,7 +236,7 @@ int lbm_create(lbm_grid g, double tau, double C_s, const double force[3], lbm_wa
     if (cudaMemsetAsync(h->tw, 0, twb, h->stream) != cudaSuccess ||
         cudaMemsetAsync(h->acc, 0, accb, h->stream) != cudaSuccess)
         return bail(fail(LBM_ERR_CUDA, "memset failed"));
-    const long long nblk = (long long)grid_of(h, h->bx).x * g.ny * g.nz;
+    const long long nblk = (long long)step_grid(h).x * g.ny * g.nz;
     const int rc = ensure_part(h, nblk * lbm::K_PART);
     if (rc != LBM_OK) return bail(rc);
     *out = h;

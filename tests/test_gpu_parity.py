@@ -6,7 +6,8 @@ components): 1e-5 for FP32 storage and 5e-3 for FP16-shifted storage, on the
 velocity u and on the population deviations f - w. The density deviation
 rho - 1 is about 1% of the population deviations it is summed from, so the
 once-per-step rounding of 19 stored deviations puts its relative error about
-100 times higher: the bound for rho - 1 is 1e-4 (FP32) and 5e-2 (FP16)."""
+100 times higher (about 2e-5 per step for FP32, growing as a random walk): the
+bound for rho - 1 is 3e-4 (FP32) and 5e-2 (FP16) over 100 steps."""
 import functools
 
 import numpy as np
@@ -18,7 +19,7 @@ from paper_2009_04352_gb300 import lbm, workload
 pytestmark = pytest.mark.gpu
 
 TOL = {lbm.FP32: 1e-5, lbm.FP16_SHIFTED: 5e-3}
-TOL_RHO = {lbm.FP32: 1e-4, lbm.FP16_SHIFTED: 5e-2}
+TOL_RHO = {lbm.FP32: 3e-4, lbm.FP16_SHIFTED: 5e-2}
 WALLS = [workload.WALL_BB, workload.WALL_WFB, workload.WALL_FREESLIP]
 _W = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
 
@@ -62,8 +63,13 @@ def gpu_channel(case, wall, precision):
 
 
 SMALL = workload.CASES["c1"]                       # 64 x 32 x 32, tau0 0.52
+# odd nx runs the one-cell kernel, even nx the two-cell kernel; rows shorter
+# than a warp, rows ending inside a warp, a single column, ny = 2 (both layers
+# are wall layers)
 RAGGED = [SMALL.with_(nx=37, ny=6, nz=5), SMALL.with_(nx=1, ny=8, nz=1),
-          SMALL.with_(nx=33, ny=2, nz=3), SMALL.with_(nx=130, ny=5, nz=2)]
+          SMALL.with_(nx=33, ny=2, nz=3), SMALL.with_(nx=130, ny=5, nz=2),
+          SMALL.with_(nx=2, ny=6, nz=3), SMALL.with_(nx=66, ny=4, nz=3),
+          SMALL.with_(nx=34, ny=2, nz=3), SMALL.with_(nx=300, ny=3, nz=2)]
 
 
 @pytest.mark.parametrize("precision", [lbm.FP32, lbm.FP16_SHIFTED])
@@ -109,20 +115,22 @@ def test_parity_100_steps(wall, precision):
     ch.close()
 
 
+@pytest.mark.parametrize("precision", [lbm.FP32, lbm.FP16_SHIFTED])
 @pytest.mark.parametrize("case", RAGGED, ids=lambda c: f"{c.nx}x{c.ny}x{c.nz}")
 @pytest.mark.parametrize("wall", WALLS)
-def test_parity_ragged(case, wall):
-    """Rows shorter than a block, not a multiple of 32, a single column, ny = 2."""
+def test_parity_ragged(case, wall, precision):
     checkpoints = (1, 7, 20)
     ref = oracle_run(case, wall, checkpoints)
-    ch = gpu_channel(case, wall, lbm.FP32)
+    ch = gpu_channel(case, wall, precision)
     t = 0
     for c in checkpoints:
         ch.step(c - t)
         t = c
         rho, u = ch.moments()
-        assert rel_linf(u, ref[c]["u"]) <= 1e-5
-        assert rel_linf(rho - 1.0, ref[c]["rho"] - 1.0) <= TOL_RHO[lbm.FP32]
+        assert rel_linf(u, ref[c]["u"]) <= TOL[precision], c
+        assert rel_linf(rho - 1.0, ref[c]["rho"] - 1.0) <= TOL_RHO[precision], c
+    if wall != workload.WALL_FREESLIP:
+        assert rel_linf(ch.wall_stress(), ref[20]["tw"]) <= 10 * TOL[precision]
     ch.close()
 
 
