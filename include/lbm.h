@@ -85,6 +85,20 @@ typedef enum {
     LBM_PULL2 = 0          /* two lattices, gather from neighbours, write own cell */
 } lbm_layout;
 
+/* Form of the fused step kernel (all compute the same update).
+ *   CELL: one thread per cell, any grid.
+ *   PAIR: two cells per thread, 2-wide loads and packed FP32 math; even nx.
+ *   TMA:  two cells per thread, each warp streams its 64-cell row segments
+ *         into shared memory with bulk asynchronous copies (mbarrier ring of
+ *         3 stages); nx a multiple of 64.
+ *   AUTO: the fastest form the grid allows (TMA, else PAIR, else CELL). */
+typedef enum {
+    LBM_KERNEL_AUTO = 0,
+    LBM_KERNEL_CELL = 1,
+    LBM_KERNEL_PAIR = 2,
+    LBM_KERNEL_TMA = 3
+} lbm_kernel;
+
 typedef struct lbm_handle lbm_handle;
 
 /* Create a lattice at rest (f_a = w_a, rho = 1, u = 0).
@@ -132,6 +146,14 @@ int lbm_step(lbm_handle *h, int n);
 /* Number of steps taken since the last (re)initialisation. */
 long long lbm_get_step(lbm_handle *h);
 
+/* Choose the step kernel form (lbm_kernel). Synchronises the stream; returns
+ * LBM_ERR_ARG if the grid does not allow the form. lbm_create selects AUTO.
+ * The populations and statistics are kept; only the launch changes. */
+int lbm_set_kernel(lbm_handle *h, int kernel);
+
+/* The kernel form in use (never LBM_KERNEL_AUTO), -1 for a NULL handle. */
+int lbm_get_kernel(lbm_handle *h);
+
 /* Density rho [nz][ny][nx] and velocity u [3][nz][ny][nx] of the current
  * populations (Eq. 2 with the Guo half-force shift, u = (sum e f + F/2)/rho),
  * FP32. on_device != 0: rho and u are device pointers and the call is
@@ -160,7 +182,9 @@ int lbm_plane_stats(lbm_handle *h, double *out, double *wall_out, long long *n_s
  * synchronises). Returns LBM_ERR_DIVERGED if any sum is NaN or Inf. */
 int lbm_conservation(lbm_handle *h, double *out);
 
-/* Block until all work queued on the handle's stream has finished. */
+/* Block until all work queued on the handle's stream has finished. Returns
+ * LBM_ERR_CUDA if a wait inside the pipelined kernel timed out (the kernel then
+ * stops early and leaves the step incomplete). */
 int lbm_sync(lbm_handle *h);
 
 /* Free every device resource of the handle. NULL is ignored. */

@@ -10,7 +10,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblbm.so")
 SOURCES = ["lbm.cu"]
-HEADERS = ["lbm_device.cuh", "lbm_kernels.cuh", "lbm_pair.cuh"]
+HEADERS = ["lbm_device.cuh", "lbm_kernels.cuh", "lbm_pair.cuh", "lbm_tma.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -5,8 +5,10 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
+
 #include "lbm.h"
-#include "lbm_pair.cuh"
+#include "lbm_tma.cuh"
 
 namespace {
 
@@ -49,8 +51,11 @@ struct lbm_handle {
     long long part_len;          // doubles
     double *acc;                 // [ny][K_STATS] then [2][K_WALL]
     long long nsamples;
-    int bx;                      // threads per block along x
+    int bx;                      // threads per block along x (one-cell / two-cell kernels)
     bool pair;                   // two cells per thread (even nx)
+    int kernel;                  // LBM_KERNEL_* in use (never AUTO)
+    int tma_grid;                // CTAs of the warp-pipelined kernel
+    int *err;                    // device flag set by a timed-out pipeline wait
     cudaGraphExec_t chunk[2];    // kGraphSteps plain steps starting from cur = 0 / 1
 };
 
@@ -63,8 +68,89 @@ dim3 grid_of(const lbm_handle *h, int bx) { return dim3((h->g.nx + bx - 1) / bx,
 // grid of the step kernel: one thread per cell, or per x-pair for even nx
 dim3 step_grid(const lbm_handle *h)
 {
-    const int per_row = h->pair ? h->g.nx / 2 : h->g.nx;
+    const int per_row = h->kernel == LBM_KERNEL_CELL ? h->g.nx : h->g.nx / 2;
     return dim3((per_row + h->bx - 1) / h->bx, h->g.ny, h->g.nz);
+}
+
+int select_kernel(lbm_handle *h, int kernel)
+{
+    const bool even = (h->g.nx % 2) == 0;
+    const bool seg = (h->g.nx % lbm::SEG) == 0;
+    if (kernel == LBM_KERNEL_AUTO) kernel = seg ? LBM_KERNEL_TMA : (even ? LBM_KERNEL_PAIR : LBM_KERNEL_CELL);
+    if (kernel == LBM_KERNEL_PAIR && !even) return fail(LBM_ERR_ARG, "two-cell kernel needs an even nx");
+    if (kernel == LBM_KERNEL_TMA && !seg) return fail(LBM_ERR_ARG, "pipelined kernel needs nx a multiple of 64");
+    if (kernel < LBM_KERNEL_CELL || kernel > LBM_KERNEL_TMA) return fail(LBM_ERR_ARG, "unknown kernel");
+    h->kernel = kernel;
+    const int per_row = kernel == LBM_KERNEL_CELL ? h->g.nx : h->g.nx / 2;
+    h->bx = per_row >= 128 ? 128 : (per_row > 32 ? 64 : 32);   // <= the kernels' launch bound of 128
+    if (kernel == LBM_KERNEL_TMA) {
+        int dev = 0, sms = 0, per_sm = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        if (h->precision == LBM_FP16_SHIFTED) {
+            const int sm = lbm::tma_smem_bytes<__half>();
+            CK(cudaFuncSetAttribute(lbm::k_step_tma<__half, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+            CK(cudaFuncSetAttribute(lbm::k_step_tma<__half, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lbm::k_step_tma<__half, false>,
+                                                             lbm::TMA_WARPS * 32, sm));
+        } else {
+            const int sm = lbm::tma_smem_bytes<float>();
+            CK(cudaFuncSetAttribute(lbm::k_step_tma<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+            CK(cudaFuncSetAttribute(lbm::k_step_tma<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lbm::k_step_tma<float, false>,
+                                                             lbm::TMA_WARPS * 32, sm));
+        }
+        if (per_sm < 1) return fail(LBM_ERR_CUDA, "pipelined kernel does not fit on an SM");
+        h->tma_grid = sms * per_sm;
+    }
+    // captured graphs hold the old launch configuration
+    for (int i = 0; i < 2; ++i)
+        if (h->chunk[i]) {
+            cudaGraphExecDestroy(h->chunk[i]);
+            h->chunk[i] = nullptr;
+        }
+    return LBM_OK;
+}
+
+int check_err(lbm_handle *h)
+{
+    int e = 0;
+    CK(cudaMemcpyAsync(&e, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (e) return fail(LBM_ERR_CUDA, "a pipeline wait in the step kernel timed out");
+    return LBM_OK;
+}
+
+// block partials of one sampled step, per wall-normal plane
+long long partials_per_plane(const lbm_handle *h)
+{
+    if (h->kernel == LBM_KERNEL_TMA) return (long long)(h->g.nx / lbm::SEG) * h->g.nz;
+    return (long long)step_grid(h).x * h->g.nz;
+}
+
+int launch_tma(lbm_handle *h, cudaStream_t s, int src, bool stats)
+{
+    const void *a = h->f[src];
+    void *b = h->f[src ^ 1];
+    const dim3 grid(h->tma_grid), block(lbm::TMA_WARPS * 32);
+    if (h->precision == LBM_FP16_SHIFTED) {
+        const int sm = lbm::tma_smem_bytes<__half>();
+        if (stats)
+            lbm::k_step_tma<__half, true><<<grid, block, sm, s>>>((const __half *)a, (__half *)b, h->g, h->p, h->tw,
+                                                                  h->part, h->err);
+        else
+            lbm::k_step_tma<__half, false><<<grid, block, sm, s>>>((const __half *)a, (__half *)b, h->g, h->p, h->tw,
+                                                                   h->part, h->err);
+    } else {
+        const int sm = lbm::tma_smem_bytes<float>();
+        if (stats)
+            lbm::k_step_tma<float, true><<<grid, block, sm, s>>>((const float *)a, (float *)b, h->g, h->p, h->tw,
+                                                                 h->part, h->err);
+        else
+            lbm::k_step_tma<float, false><<<grid, block, sm, s>>>((const float *)a, (float *)b, h->g, h->p, h->tw,
+                                                                  h->part, h->err);
+    }
+    return LBM_OK;
 }
 
 int launch_step(lbm_handle *h, cudaStream_t s, int src, bool stats)
@@ -72,14 +158,16 @@ int launch_step(lbm_handle *h, cudaStream_t s, int src, bool stats)
     const dim3 grid = step_grid(h), block(h->bx);
     const void *a = h->f[src];
     void *b = h->f[src ^ 1];
-    if (h->pair && h->precision == LBM_FP16_SHIFTED) {
+    if (h->kernel == LBM_KERNEL_TMA) {
+        launch_tma(h, s, src, stats);
+    } else if (h->kernel == LBM_KERNEL_PAIR && h->precision == LBM_FP16_SHIFTED) {
         if (stats)
             lbm::k_step_pair<__half, true><<<grid, block, 0, s>>>((const __half *)a, (__half *)b, h->g, h->p, h->tw,
                                                                   h->part);
         else
             lbm::k_step_pair<__half, false><<<grid, block, 0, s>>>((const __half *)a, (__half *)b, h->g, h->p, h->tw,
                                                                    h->part);
-    } else if (h->pair) {
+    } else if (h->kernel == LBM_KERNEL_PAIR) {
         if (stats)
             lbm::k_step_pair<float, true><<<grid, block, 0, s>>>((const float *)a, (float *)b, h->g, h->p, h->tw, h->part);
         else
@@ -98,7 +186,7 @@ int launch_step(lbm_handle *h, cudaStream_t s, int src, bool stats)
     }
     CK_LAUNCH();
     if (stats) {
-        const long long per_plane = (long long)grid.x * h->g.nz;
+        const long long per_plane = partials_per_plane(h);
         lbm::k_reduce_planes<<<h->g.ny, 256, 0, s>>>(h->part, per_plane, h->g.ny, h->acc,
                                                      h->acc + (long long)h->g.ny * lbm::K_STATS);
         CK_LAUNCH();
@@ -206,11 +294,6 @@ int lbm_create(lbm_grid g, double tau, double C_s, const double force[3], lbm_wa
     h->layout = layout;
     h->stream = (cudaStream_t)cuda_stream;
     h->pair = (g.nx % 2) == 0;
-    {
-        // threads per block (<= the kernels' launch bound of 128), a multiple of 32
-        const int per_row = h->pair ? g.nx / 2 : g.nx;
-        h->bx = per_row >= 128 ? 128 : (per_row > 32 ? 64 : 32);
-    }
 
     auto bail = [&](int rc) {
         lbm_destroy(h);
@@ -236,8 +319,17 @@ int lbm_create(lbm_grid g, double tau, double C_s, const double force[3], lbm_wa
     if (cudaMemsetAsync(h->tw, 0, twb, h->stream) != cudaSuccess ||
         cudaMemsetAsync(h->acc, 0, accb, h->stream) != cudaSuccess)
         return bail(fail(LBM_ERR_CUDA, "memset failed"));
-    const long long nblk = (long long)step_grid(h).x * g.ny * g.nz;
-    const int rc = ensure_part(h, nblk * lbm::K_PART);
+    if (cudaMalloc((void **)&h->err, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(LBM_ERR_OOM, "cannot allocate the error flag"));
+    }
+    if (cudaMemsetAsync(h->err, 0, sizeof(int), h->stream) != cudaSuccess) return bail(fail(LBM_ERR_CUDA, "memset"));
+    int rc = select_kernel(h, LBM_KERNEL_AUTO);
+    if (rc != LBM_OK) return bail(rc);
+    // partial sums: enough for any kernel form on this grid
+    const long long nblk = std::max((long long)((g.nx + 31) / 32) * g.ny * g.nz,
+                                    (long long)(g.nx / lbm::SEG) * g.ny * g.nz);
+    rc = ensure_part(h, nblk * lbm::K_PART);
     if (rc != LBM_OK) return bail(rc);
     *out = h;
     return LBM_OK;
@@ -294,8 +386,7 @@ int lbm_populations(lbm_handle *h, double *host_out)
     if (rc != LBM_OK) return rc;
     CK(cudaMemcpyAsync(host_out, d, b, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaFreeAsync(d, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
-    return LBM_OK;
+    return check_err(h);
 }
 
 int lbm_set_stats_every(lbm_handle *h, int every)
@@ -347,6 +438,15 @@ int lbm_step(lbm_handle *h, int n)
 }
 
 long long lbm_get_step(lbm_handle *h) { return h ? h->step : -1; }
+
+int lbm_set_kernel(lbm_handle *h, int kernel)
+{
+    if (!h) return fail(LBM_ERR_ARG, "NULL handle");
+    CK(cudaStreamSynchronize(h->stream));
+    return select_kernel(h, kernel);
+}
+
+int lbm_get_kernel(lbm_handle *h) { return h ? h->kernel : -1; }
 
 int lbm_moments(lbm_handle *h, float *rho, float *u, int on_device)
 {
@@ -406,7 +506,8 @@ int lbm_conservation(lbm_handle *h, double *out)
     CK_LAUNCH();
     CK(cudaMemcpyAsync(out, d + nblk * 4, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaFreeAsync(d, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
+    rc = check_err(h);
+    if (rc != LBM_OK) return rc;
     // the partials are deviations from the rest state: add sum w = 1 per cell
     out[0] += (double)h->g.nx * h->g.ny * h->g.nz;
     for (int k = 0; k < 4; ++k)
@@ -418,7 +519,7 @@ int lbm_sync(lbm_handle *h)
 {
     if (!h) return fail(LBM_ERR_ARG, "NULL handle");
     CK(cudaStreamSynchronize(h->stream));
-    return LBM_OK;
+    return check_err(h);
 }
 
 void lbm_destroy(lbm_handle *h)
@@ -432,6 +533,7 @@ void lbm_destroy(lbm_handle *h)
     if (h->part) cudaFree(h->part);
     if (h->tw) cudaFree(h->tw);
     if (h->acc) cudaFree(h->acc);
+    if (h->err) cudaFree(h->err);
     if (h->cap) cudaStreamDestroy(h->cap);
     delete h;
 }

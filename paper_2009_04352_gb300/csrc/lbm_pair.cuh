@@ -92,38 +92,42 @@ struct PairState {
     float2 rho, ux, uy, uz;
 };
 
-// collide() of lbm_kernels.cuh for two cells (in place: f becomes f*).
+// collide() of lbm_kernels.cuh for two cells (in place: f becomes f*),
+// organised around the opposite pairs k = 0..8 (directions 2k+1, 2k+2):
+// s_k = f_a + f_b and d_k = f_a - f_b carry all moments the update needs,
+//   drho = f_0 + sum s,  j = sum e_k d_k,  Pi_ab = sum e_k,a e_k,b s_k,
+// and the update of the pair is  delta_a = de + dd,  delta_b = de - dd  with
+//   de = omega w (S0 + 9/2 rho (e.u)^2) - 3 w gk u.F + 9 w gk (e.u)(e.F) - omega s / 2
+//   dd = 3 omega w rho (e.u) + 3 w gk (e.F) - omega d / 2.
 __device__ __forceinline__ PairState collide_pair(float2 (&f)[Q], const Phys &p)
 {
     PairState c;
-    const float2 drho = add2(add2(add2(add2(f[0], f[1]), add2(f[2], f[3])), add2(add2(f[4], f[5]), add2(f[6], f[7]))),
-                             add2(add2(add2(f[8], f[9]), add2(f[10], f[11])),
-                                  add2(add2(add2(f[12], f[13]), add2(f[14], f[15])),
-                                       add2(add2(f[16], f[17]), f[18]))));
-    const float2 jx = add2(add2(sub2(f[1], f[2]), sub2(f[7], f[8])),
-                           add2(add2(sub2(f[9], f[10]), sub2(f[13], f[14])), sub2(f[15], f[16])));
-    const float2 jy = add2(add2(sub2(f[3], f[4]), sub2(f[7], f[8])),
-                           add2(add2(sub2(f[11], f[12]), sub2(f[14], f[13])), sub2(f[17], f[18])));
-    const float2 jz = add2(add2(sub2(f[5], f[6]), sub2(f[9], f[10])),
-                           add2(add2(sub2(f[11], f[12]), sub2(f[16], f[15])), sub2(f[18], f[17])));
+    float2 sk[9], dk[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        sk[k] = add2(f[2 * k + 1], f[2 * k + 2]);
+        dk[k] = sub2(f[2 * k + 1], f[2 * k + 2]);
+    }
+    const float2 drho = add2(add2(add2(f[0], sk[0]), add2(sk[1], sk[2])),
+                             add2(add2(add2(sk[3], sk[4]), add2(sk[5], sk[6])), add2(sk[7], sk[8])));
+    const float2 jx = add2(add2(dk[0], dk[3]), add2(add2(dk[4], dk[6]), dk[7]));
+    const float2 jy = add2(add2(dk[1], dk[3]), add2(sub2(dk[5], dk[6]), dk[8]));
+    const float2 jz = sub2(add2(add2(dk[2], dk[4]), dk[5]), add2(dk[7], dk[8]));
+    float2 pxx = add2(add2(sk[0], sk[3]), add2(add2(sk[4], sk[6]), sk[7]));
+    float2 pyy = add2(add2(sk[1], sk[3]), add2(add2(sk[5], sk[6]), sk[8]));
+    float2 pzz = add2(add2(sk[2], sk[4]), add2(add2(sk[5], sk[7]), sk[8]));
+    float2 pxy = sub2(sk[3], sk[6]);
+    float2 pxz = sub2(sk[4], sk[7]);
+    float2 pyz = sub2(sk[5], sk[8]);
+
     c.rho = add2(bc(1.f), drho);
     const float2 idev = make_float2(-drho.x / c.rho.x, -drho.y / c.rho.y);   // 1/rho - 1
-    const float2 jfx = fma2(bc(0.5f), bc(p.Fx), jx), jfy = fma2(bc(0.5f), bc(p.Fy), jy),
-                 jfz = fma2(bc(0.5f), bc(p.Fz), jz);
+    const float2 jfx = add2(jx, bc(0.5f * p.Fx)), jfy = add2(jy, bc(0.5f * p.Fy)), jfz = add2(jz, bc(0.5f * p.Fz));
     c.ux = fma2(jfx, idev, jfx);
     c.uy = fma2(jfy, idev, jfy);
     c.uz = fma2(jfz, idev, jfz);
     const float2 rho = c.rho, ux = c.ux, uy = c.uy, uz = c.uz;
 
-    float2 pxx = add2(add2(add2(f[1], f[2]), add2(f[7], f[8])),
-                      add2(add2(add2(f[9], f[10]), add2(f[13], f[14])), add2(f[15], f[16])));
-    float2 pyy = add2(add2(add2(f[3], f[4]), add2(f[7], f[8])),
-                      add2(add2(add2(f[11], f[12]), add2(f[13], f[14])), add2(f[17], f[18])));
-    float2 pzz = add2(add2(add2(f[5], f[6]), add2(f[9], f[10])),
-                      add2(add2(add2(f[11], f[12]), add2(f[15], f[16])), add2(f[17], f[18])));
-    float2 pxy = sub2(add2(f[7], f[8]), add2(f[13], f[14]));
-    float2 pxz = sub2(add2(f[9], f[10]), add2(f[15], f[16]));
-    float2 pyz = sub2(add2(f[11], f[12]), add2(f[17], f[18]));
     const float2 cd = mul2(drho, bc(1.f / 3.f));
     const float2 rux = mul2(rho, ux), ruy = mul2(rho, uy), ruz = mul2(rho, uz);
     pxx = sub2(pxx, fma2(rux, ux, cd));
@@ -143,33 +147,33 @@ __device__ __forceinline__ PairState collide_pair(float2 (&f)[Q], const Phys &p)
         omega = make_float2(1.f / tx, 1.f / ty);
     }
     const float2 gk = fma2(bc(-0.5f), omega, bc(1.f));
+    const float2 hw = mul2(bc(-0.5f), omega);                              // -omega / 2
     const float2 usq = fma2(ux, ux, fma2(uy, uy, mul2(uz, uz)));
     const float2 uF = fma2(ux, bc(p.Fx), fma2(uy, bc(p.Fy), mul2(uz, bc(p.Fz))));
     const float2 S0 = fma2(bc(-1.5f), mul2(rho, usq), drho);
-    const float2 r45 = mul2(bc(4.5f), rho), r3 = mul2(bc(3.f), rho);
+    const float2 oS = sub2(mul2(omega, S0), mul2(mul2(bc(3.f), gk), uF));  // omega S0 - 3 gk u.F
+    const float2 oR45 = mul2(omega, mul2(bc(4.5f), rho));                // 4.5 omega rho
+    const float2 oR3 = mul2(omega, mul2(bc(3.f), rho));                  // 3 omega rho
     const float2 g9 = mul2(bc(9.f), gk), g3 = mul2(bc(3.f), gk);
-    const float2 ng3uF = mul2(bc(-1.f), mul2(g3, uF));
+    // class constants (w = 1/18 axis, 1/36 diagonal)
+    const float2 Ca = mul2(bc(1.f / 18.f), oS), Cd = mul2(bc(1.f / 36.f), oS);
+    const float2 Aa = mul2(bc(1.f / 18.f), oR45), Ad = mul2(bc(1.f / 36.f), oR45);
+    const float2 Da = mul2(bc(1.f / 18.f), oR3), Dd = mul2(bc(1.f / 36.f), oR3);
 
     float2 mass = bc(0.f), mx = bc(0.f), my = bc(0.f), mz = bc(0.f);
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
         const int a = 2 * k + 1;
-        const float2 w = bc((float)w_of(a));
+        const bool axis = k < 3;
+        const float wk = axis ? 1.f / 18.f : 1.f / 36.f;
         float2 eu = bc(0.f);
         if (ex_of(a)) eu = ex_of(a) > 0 ? add2(eu, ux) : sub2(eu, ux);
         if (ey_of(a)) eu = ey_of(a) > 0 ? add2(eu, uy) : sub2(eu, uy);
         if (ez_of(a)) eu = ez_of(a) > 0 ? add2(eu, uz) : sub2(eu, uz);
-        const float eFs = ex_of(a) * p.Fx + ey_of(a) * p.Fy + ez_of(a) * p.Fz;
-        const float2 eF = bc(eFs);
-        const float2 fe = mul2(bc(0.5f), add2(f[a], f[a + 1]));
-        const float2 fo = mul2(bc(0.5f), sub2(f[a], f[a + 1]));
-        // de = omega (w (S0 + 4.5 rho eu^2) - fe) + w (9 gk eu eF - 3 gk uF)
-        const float2 eqe = mul2(w, fma2(mul2(r45, eu), eu, S0));
-        const float2 fre = mul2(w, fma2(mul2(g9, eu), eF, ng3uF));
-        const float2 de = fma2(omega, sub2(eqe, fe), fre);
-        // dd = omega (3 w rho eu - fo) + 3 w gk eF
-        const float2 eqo = mul2(w, mul2(r3, eu));
-        const float2 dd = fma2(omega, sub2(eqo, fo), mul2(w, mul2(g3, eF)));
+        const float eFs = wk * (ex_of(a) * p.Fx + ey_of(a) * p.Fy + ez_of(a) * p.Fz);   // w e.F
+        const float2 Gk = mul2(g9, bc(eFs)), Hk = mul2(g3, bc(eFs));
+        const float2 de = fma2(hw, sk[k], fma2(fma2(axis ? Aa : Ad, eu, Gk), eu, axis ? Ca : Cd));
+        const float2 dd = fma2(hw, dk[k], fma2(axis ? Da : Dd, eu, Hk));
         mass = add2(mass, de);
         if (ex_of(a)) mx = ex_of(a) > 0 ? add2(mx, dd) : sub2(mx, dd);
         if (ey_of(a)) my = ey_of(a) > 0 ? add2(my, dd) : sub2(my, dd);

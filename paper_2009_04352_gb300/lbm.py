@@ -28,6 +28,7 @@ LBM_ERR_DIVERGED = -4
 LBM_ERR_STATE = -5
 
 WALL_BB, WALL_WFB, WALL_FREESLIP = 0, 1, 2
+KERNEL_AUTO, KERNEL_CELL, KERNEL_PAIR, KERNEL_TMA = 0, 1, 2, 3
 FP32, FP16_SHIFTED = 0, 1
 PULL2 = 0
 
@@ -63,6 +64,8 @@ _SIGNATURES = {
     "lbm_set_stats_every": (C.c_int, [_VP, C.c_int]),
     "lbm_step": (C.c_int, [_VP, C.c_int]),
     "lbm_get_step": (C.c_longlong, [_VP]),
+    "lbm_set_kernel": (C.c_int, [_VP, C.c_int]),
+    "lbm_get_kernel": (C.c_int, [_VP]),
     "lbm_moments": (C.c_int, [_VP, _VP, _VP, C.c_int]),
     "lbm_wall_stress": (C.c_int, [_VP, _VP, C.c_int]),
     "lbm_plane_stats": (C.c_int, [_VP, _DP, _DP, C.POINTER(C.c_longlong), C.c_int]),
@@ -154,6 +157,14 @@ def lbm_get_step(h):
     return int(lib().lbm_get_step(h))
 
 
+def lbm_set_kernel(h, kernel):
+    _check(lib().lbm_set_kernel(h, int(kernel)))
+
+
+def lbm_get_kernel(h):
+    return int(lib().lbm_get_kernel(h))
+
+
 def lbm_moments(h, rho_ptr, u_ptr, on_device):
     _check(lib().lbm_moments(h, C.c_void_p(rho_ptr), C.c_void_p(u_ptr), int(on_device)))
 
@@ -237,6 +248,13 @@ class Channel:
     @property
     def step_count(self):
         return lbm_get_step(self._h)
+
+    @property
+    def kernel(self):
+        return lbm_get_kernel(self._h)
+
+    def set_kernel(self, kernel):
+        lbm_set_kernel(self._h, kernel)
 
     def moments(self, device=False):
         """(rho [nz,ny,nx], u [3,nz,ny,nx]) as FP32 numpy arrays, or torch CUDA

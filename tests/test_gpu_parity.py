@@ -56,8 +56,10 @@ def oracle_run(case, wall, checkpoints, stats_every=0):
     return out
 
 
-def gpu_channel(case, wall, precision):
+def gpu_channel(case, wall, precision, kernel=lbm.KERNEL_AUTO):
     ch = lbm.Channel.from_case(case, precision=precision, wall=wall)
+    if kernel != lbm.KERNEL_AUTO:
+        ch.set_kernel(kernel)
     ch.init_channel(workload.u_mean_profile(case), workload.noise_amplitude(case), case.seed)
     return ch
 
@@ -69,7 +71,10 @@ SMALL = workload.CASES["c1"]                       # 64 x 32 x 32, tau0 0.52
 RAGGED = [SMALL.with_(nx=37, ny=6, nz=5), SMALL.with_(nx=1, ny=8, nz=1),
           SMALL.with_(nx=33, ny=2, nz=3), SMALL.with_(nx=130, ny=5, nz=2),
           SMALL.with_(nx=2, ny=6, nz=3), SMALL.with_(nx=66, ny=4, nz=3),
-          SMALL.with_(nx=34, ny=2, nz=3), SMALL.with_(nx=300, ny=3, nz=2)]
+          SMALL.with_(nx=34, ny=2, nz=3), SMALL.with_(nx=300, ny=3, nz=2),
+          SMALL.with_(nx=64, ny=2, nz=3), SMALL.with_(nx=192, ny=5, nz=2),
+          SMALL.with_(nx=128, ny=3, nz=1)]
+KERNELS = [lbm.KERNEL_TMA, lbm.KERNEL_PAIR, lbm.KERNEL_CELL]
 
 
 @pytest.mark.parametrize("precision", [lbm.FP32, lbm.FP16_SHIFTED])
@@ -85,14 +90,16 @@ def test_init_matches_oracle(precision):
     ch.close()
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("precision", [lbm.FP32, lbm.FP16_SHIFTED])
 @pytest.mark.parametrize("wall", WALLS)
-def test_parity_100_steps(wall, precision):
+def test_parity_100_steps(wall, precision, kernel):
     """64x32x32 channel, tau0 0.52, C_s 0.1, seeded log-law + 10% noise: 100 steps."""
     case = SMALL
     checkpoints = (1, 10, 50, 100)
     ref = oracle_run(case, wall, checkpoints)
-    ch = gpu_channel(case, wall, precision)
+    ch = gpu_channel(case, wall, precision, kernel)
+    assert ch.kernel == kernel
     t = 0
     worst = {}
     for c in checkpoints:
@@ -236,4 +243,41 @@ def test_full_size_bench_grid(precision):
     assert rel_linf(u, ref["u"]) <= TOL[precision]
     assert rel_linf(rho - 1.0, ref["rho"] - 1.0) <= TOL_RHO[precision]
     assert rel_linf(ch.wall_stress(), ref["tw"]) <= 10 * TOL[precision]
+    ch.close()
+
+
+@pytest.mark.parametrize("precision", [lbm.FP32, lbm.FP16_SHIFTED])
+def test_pipelined_and_pair_kernels_agree_bitwise(precision):
+    """The warp-pipelined and the two-cell kernels share the collision code and
+    must give identical bits; statistics included."""
+    case = SMALL.with_(nx=128, ny=8, nz=6)
+    a = gpu_channel(case, workload.WALL_WFB, precision, lbm.KERNEL_TMA)
+    b = gpu_channel(case, workload.WALL_WFB, precision, lbm.KERNEL_PAIR)
+    for ch in (a, b):
+        ch.set_stats_every(4)
+        ch.step(37)
+    assert np.array_equal(a.populations(), b.populations())
+    assert np.array_equal(a.wall_stress(), b.wall_stress())
+    sa, wa, na = a.plane_stats()
+    sb, wb, nb = b.plane_stats()
+    assert na == nb == 10
+    assert np.allclose(sa, sb, rtol=1e-12, atol=1e-15) and np.allclose(wa, wb, rtol=1e-12, atol=1e-18)
+    a.close()
+    b.close()
+
+
+def test_kernel_selection_rules():
+    case = SMALL.with_(nx=66, ny=4, nz=2)
+    ch = lbm.Channel.from_case(case)
+    assert ch.kernel == lbm.KERNEL_PAIR
+    with pytest.raises(lbm.LbmError):
+        ch.set_kernel(lbm.KERNEL_TMA)
+    ch.close()
+    ch = lbm.Channel.from_case(case.with_(nx=37))
+    assert ch.kernel == lbm.KERNEL_CELL
+    with pytest.raises(lbm.LbmError):
+        ch.set_kernel(lbm.KERNEL_PAIR)
+    ch.close()
+    ch = lbm.Channel.from_case(case.with_(nx=128))
+    assert ch.kernel == lbm.KERNEL_TMA
     ch.close()
