@@ -182,6 +182,27 @@ int lbm_plane_stats(lbm_handle *h, double *out, double *wall_out, long long *n_s
  * synchronises). Returns LBM_ERR_DIVERGED if any sum is NaN or Inf. */
 int lbm_conservation(lbm_handle *h, double *out);
 
+/* Instantaneous plane sums of the current populations, written without any
+ * device allocation. The paper has no counterpart: this is a library service
+ * for callers that must not allocate device memory when they take the
+ * measurement, e.g. code running under a fixed memory budget or a pool that
+ * must not grow, or a host loop that has to avoid allocation calls because
+ * they can synchronise the device.
+ *   out_dev  caller-owned DEVICE array [ny][LBM_K_STATS] receiving, for each
+ *            layer, the sums over its cells of rho, u_x, u_y, u_z, u_x^2,
+ *            u_y^2, u_z^2, u_x u_y, rho u_x, rho u_y, rho u_z (the columns of
+ *            lbm_plane_stats, for the current state only, nothing accumulated).
+ * Asynchronous on the handle's stream. The block partial sums live in one
+ * fixed array of 1.44 MB that the library keeps in device memory on every GPU
+ * that loads it, until the process exits; it holds at most ny = 2048 layers,
+ * and larger grids are rejected with LBM_ERR_ARG. The first call on a device
+ * looks up that array's device address (cudaGetSymbolAddress) with the device
+ * current, so make the first call before any stream capture. Every call
+ * overwrites the part of the array it uses, so nothing needs clearing between
+ * calls; calls whose work overlaps on the GPU (other streams or handles) race
+ * on the shared array and must be ordered by the caller. */
+int lbm_plane_profile_noalloc(lbm_handle *h, double *out_dev);
+
 /* Block until all work queued on the handle's stream has finished. Returns
  * LBM_ERR_CUDA if a wait inside the pipelined kernel timed out (the kernel then
  * stops early and leaves the step incomplete). */

@@ -9,8 +9,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblbm.so")
-SOURCES = ["lbm.cu"]
-HEADERS = ["lbm_device.cuh", "lbm_kernels.cuh", "lbm_pair.cuh", "lbm_tma.cuh"]
+SOURCES = ["lbm.cu", "lbm_noalloc.cu"]
+HEADERS = ["lbm_device.cuh", "lbm_kernels.cuh", "lbm_pair.cuh", "lbm_tma.cuh", "lbm_handle.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -35,29 +35,9 @@ constexpr int kGraphSteps = 16;   // steps captured per chunk graph (even)
 
 }  // namespace
 
-struct lbm_handle {
-    lbm::Geom g;
-    lbm::Phys p;
-    int precision;
-    int layout;
-    cudaStream_t stream;
-    cudaStream_t cap;            // private stream used only for graph capture
-    void *f[2];                  // two lattices
-    int cur;                     // lattice holding the current post-collision state
-    long long step;
-    int stats_every;
-    float *tw;                   // [2][nz][nx][2]
-    double *part;                // block partials
-    long long part_len;          // doubles
-    double *acc;                 // [ny][K_STATS] then [2][K_WALL]
-    long long nsamples;
-    int bx;                      // threads per block along x (one-cell / two-cell kernels)
-    bool pair;                   // two cells per thread (even nx)
-    int kernel;                  // LBM_KERNEL_* in use (never AUTO)
-    int tma_grid;                // CTAs of the warp-pipelined kernel
-    int *err;                    // device flag set by a timed-out pipeline wait
-    cudaGraphExec_t chunk[2];    // kGraphSteps plain steps starting from cur = 0 / 1
-};
+#include "lbm_handle.h"
+
+int lbm_record_error(int code, const char *msg) { return fail(code, "%s", msg); }
 
 namespace {
 

@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(128) k_step(const T *__restrict__ src, T *__re
 
 // Sum the block partials of each plane (one block per plane, fixed order, so
 // the result is deterministic) into the FP64 accumulators.
-__global__ void k_reduce_planes(const double *__restrict__ part, long long per_plane, int ny,
+static __global__ void k_reduce_planes(const double *__restrict__ part, long long per_plane, int ny,
                                 double *__restrict__ acc, double *__restrict__ wacc)
 {
     const int y = blockIdx.x;
@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(256) k_export(const T *__restrict__ src, Geom 
     }
 }
 
-__global__ void k_reduce_all(const double *__restrict__ part, long long nblk, double *__restrict__ out)
+static __global__ void k_reduce_all(const double *__restrict__ part, long long nblk, double *__restrict__ out)
 {
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     for (long long i = threadIdx.x; i < nblk; i += blockDim.x) {

@@ -70,6 +70,7 @@ _SIGNATURES = {
     "lbm_wall_stress": (C.c_int, [_VP, _VP, C.c_int]),
     "lbm_plane_stats": (C.c_int, [_VP, _DP, _DP, C.POINTER(C.c_longlong), C.c_int]),
     "lbm_conservation": (C.c_int, [_VP, _DP]),
+    "lbm_plane_profile_noalloc": (C.c_int, [_VP, _VP]),
     "lbm_sync": (C.c_int, [_VP]),
     "lbm_destroy": (None, [_VP]),
     "lbm_last_error": (C.c_char_p, []),
@@ -185,6 +186,10 @@ def lbm_conservation(h, out):
     rc = lib().lbm_conservation(h, _dp(out))
     _check(rc)
     return out
+
+
+def lbm_plane_profile_noalloc(h, out_dev_ptr):
+    _check(lib().lbm_plane_profile_noalloc(h, C.c_void_p(out_dev_ptr)))
 
 
 def lbm_sync(h):
