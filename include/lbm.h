@@ -88,10 +88,10 @@ typedef enum {
 /* Form of the fused step kernel (all compute the same update).
  *   CELL: one thread per cell, any grid.
  *   PAIR: two cells per thread, 2-wide loads and packed FP32 math; even nx.
- *   TMA:  two cells per thread, each warp streams its 64-cell row segments
- *         into shared memory with bulk asynchronous copies (mbarrier ring of
- *         3 stages); nx a multiple of 64.
- *   AUTO: the fastest form the grid allows (TMA, else PAIR, else CELL). */
+ *   TMA:  two cells per thread; each CTA streams whole source rows into a
+ *         shared-memory ring with bulk asynchronous copies (full/empty
+ *         mbarriers, 2-4 stages); nx a multiple of 64 whose rows fit the ring.
+ *   AUTO: PAIR for even nx, else CELL. */
 typedef enum {
     LBM_KERNEL_AUTO = 0,
     LBM_KERNEL_CELL = 1,

@@ -52,11 +52,15 @@ dim3 step_grid(const lbm_handle *h)
     return dim3((per_row + h->bx - 1) / h->bx, h->g.ny, h->g.nz);
 }
 
+int configure_rows(lbm_handle *h);
+
 int select_kernel(lbm_handle *h, int kernel)
 {
     const bool even = (h->g.nx % 2) == 0;
-    const bool seg = (h->g.nx % lbm::SEG) == 0;
-    if (kernel == LBM_KERNEL_AUTO) kernel = seg ? LBM_KERNEL_TMA : (even ? LBM_KERNEL_PAIR : LBM_KERNEL_CELL);
+    const bool seg = (h->g.nx % 64) == 0;
+    // AUTO: the two-cell kernel where nx is even (measured fastest on GB300 for
+    // every benchmark grid in both storage precisions), else the one-cell kernel
+    if (kernel == LBM_KERNEL_AUTO) kernel = even ? LBM_KERNEL_PAIR : LBM_KERNEL_CELL;
     if (kernel == LBM_KERNEL_PAIR && !even) return fail(LBM_ERR_ARG, "two-cell kernel needs an even nx");
     if (kernel == LBM_KERNEL_TMA && !seg) return fail(LBM_ERR_ARG, "pipelined kernel needs nx a multiple of 64");
     if (kernel < LBM_KERNEL_CELL || kernel > LBM_KERNEL_TMA) return fail(LBM_ERR_ARG, "unknown kernel");
@@ -64,24 +68,8 @@ int select_kernel(lbm_handle *h, int kernel)
     const int per_row = kernel == LBM_KERNEL_CELL ? h->g.nx : h->g.nx / 2;
     h->bx = per_row >= 128 ? 128 : (per_row > 32 ? 64 : 32);   // <= the kernels' launch bound of 128
     if (kernel == LBM_KERNEL_TMA) {
-        int dev = 0, sms = 0, per_sm = 0;
-        CK(cudaGetDevice(&dev));
-        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        if (h->precision == LBM_FP16_SHIFTED) {
-            const int sm = lbm::tma_smem_bytes<__half>();
-            CK(cudaFuncSetAttribute(lbm::k_step_tma<__half, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-            CK(cudaFuncSetAttribute(lbm::k_step_tma<__half, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lbm::k_step_tma<__half, false>,
-                                                             lbm::TMA_WARPS * 32, sm));
-        } else {
-            const int sm = lbm::tma_smem_bytes<float>();
-            CK(cudaFuncSetAttribute(lbm::k_step_tma<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-            CK(cudaFuncSetAttribute(lbm::k_step_tma<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lbm::k_step_tma<float, false>,
-                                                             lbm::TMA_WARPS * 32, sm));
-        }
-        if (per_sm < 1) return fail(LBM_ERR_CUDA, "pipelined kernel does not fit on an SM");
-        h->tma_grid = sms * per_sm;
+        const int rc = configure_rows(h);
+        if (rc != LBM_OK) return rc;
     }
     // captured graphs hold the old launch configuration
     for (int i = 0; i < 2; ++i)
@@ -104,33 +92,93 @@ int check_err(lbm_handle *h)
 // block partials of one sampled step, per wall-normal plane
 long long partials_per_plane(const lbm_handle *h)
 {
-    if (h->kernel == LBM_KERNEL_TMA) return (long long)(h->g.nx / lbm::SEG) * h->g.nz;
+    if (h->kernel == LBM_KERNEL_TMA) return (long long)h->tma_warps * h->g.nz;
     return (long long)step_grid(h).x * h->g.nz;
+}
+
+template <typename T, int NW>
+void launch_rows_t(lbm_handle *h, cudaStream_t s, int src, bool stats)
+{
+    const T *a = (const T *)h->f[src];
+    T *b = (T *)h->f[src ^ 1];
+    const dim3 grid(h->tma_grid), block(NW * 32);
+    if (stats)
+        lbm::k_step_rows<T, true, NW><<<grid, block, h->tma_smem, s>>>(a, b, h->g, h->p, h->tw, h->part, h->err,
+                                                                        h->tma_stages);
+    else
+        lbm::k_step_rows<T, false, NW><<<grid, block, h->tma_smem, s>>>(a, b, h->g, h->p, h->tw, h->part, h->err,
+                                                                         h->tma_stages);
 }
 
 int launch_tma(lbm_handle *h, cudaStream_t s, int src, bool stats)
 {
-    const void *a = h->f[src];
-    void *b = h->f[src ^ 1];
-    const dim3 grid(h->tma_grid), block(lbm::TMA_WARPS * 32);
     if (h->precision == LBM_FP16_SHIFTED) {
-        const int sm = lbm::tma_smem_bytes<__half>();
-        if (stats)
-            lbm::k_step_tma<__half, true><<<grid, block, sm, s>>>((const __half *)a, (__half *)b, h->g, h->p, h->tw,
-                                                                  h->part, h->err);
+        if (h->tma_warps == 8)
+            launch_rows_t<__half, 8>(h, s, src, stats);
         else
-            lbm::k_step_tma<__half, false><<<grid, block, sm, s>>>((const __half *)a, (__half *)b, h->g, h->p, h->tw,
-                                                                   h->part, h->err);
+            launch_rows_t<__half, 4>(h, s, src, stats);
     } else {
-        const int sm = lbm::tma_smem_bytes<float>();
-        if (stats)
-            lbm::k_step_tma<float, true><<<grid, block, sm, s>>>((const float *)a, (float *)b, h->g, h->p, h->tw,
-                                                                 h->part, h->err);
+        if (h->tma_warps == 8)
+            launch_rows_t<float, 8>(h, s, src, stats);
         else
-            lbm::k_step_tma<float, false><<<grid, block, sm, s>>>((const float *)a, (float *)b, h->g, h->p, h->tw,
-                                                                  h->part, h->err);
+            launch_rows_t<float, 4>(h, s, src, stats);
     }
     return LBM_OK;
+}
+
+// Blocks per SM of one row-kernel instantiation with `smem` dynamic bytes.
+template <typename T, int NW>
+int rows_occupancy(int smem, int *per_sm)
+{
+    CK(cudaFuncSetAttribute(lbm::k_step_rows<T, false, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    CK(cudaFuncSetAttribute(lbm::k_step_rows<T, true, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, lbm::k_step_rows<T, false, NW>, NW * 32, smem));
+    int st = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&st, lbm::k_step_rows<T, true, NW>, NW * 32, smem));
+    *per_sm = std::min(*per_sm, st);
+    return LBM_OK;
+}
+
+// Warps per CTA, ring depth and grid of the row kernel: the most resident
+// warps per SM, then the deepest ring. Fails if even two stages do not fit.
+int configure_rows(lbm_handle *h)
+{
+    int dev = 0, sms = 0, smem_max = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CK(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    const bool half = h->precision == LBM_FP16_SHIFTED;
+    const int nw = h->g.nx >= 512 ? 8 : 4;
+    int best_warps = 0, best_stages = 0, best_per_sm = 0;
+    for (int stages = lbm::ROW_MAX_STAGES; stages >= 2; --stages) {
+        const int smem = half ? lbm::rows_smem_bytes<__half>(h->g.nx, stages)
+                              : lbm::rows_smem_bytes<float>(h->g.nx, stages);
+        if (smem > smem_max) continue;
+        int per_sm = 0, rc;
+        if (half)
+            rc = nw == 8 ? rows_occupancy<__half, 8>(smem, &per_sm) : rows_occupancy<__half, 4>(smem, &per_sm);
+        else
+            rc = nw == 8 ? rows_occupancy<float, 8>(smem, &per_sm) : rows_occupancy<float, 4>(smem, &per_sm);
+        if (rc != LBM_OK) return rc;
+        if (per_sm * nw > best_warps) {
+            best_warps = per_sm * nw;
+            best_stages = stages;
+            best_per_sm = per_sm;
+        }
+    }
+    if (best_warps == 0) return fail(LBM_ERR_ARG, "rows of this grid do not fit the pipelined kernel's shared memory");
+    h->tma_warps = nw;
+    h->tma_stages = best_stages;
+    h->tma_smem = half ? lbm::rows_smem_bytes<__half>(h->g.nx, best_stages)
+                       : lbm::rows_smem_bytes<float>(h->g.nx, best_stages);
+    h->tma_grid = sms * best_per_sm;
+    // the probe above left the attribute at the last candidate: set the chosen size
+    int per_sm = 0, rc;
+    if (half)
+        rc = nw == 8 ? rows_occupancy<__half, 8>(h->tma_smem, &per_sm) : rows_occupancy<__half, 4>(h->tma_smem, &per_sm);
+    else
+        rc = nw == 8 ? rows_occupancy<float, 8>(h->tma_smem, &per_sm) : rows_occupancy<float, 4>(h->tma_smem, &per_sm);
+    return rc;
 }
 
 int launch_step(lbm_handle *h, cudaStream_t s, int src, bool stats)
@@ -307,8 +355,7 @@ int lbm_create(lbm_grid g, double tau, double C_s, const double force[3], lbm_wa
     int rc = select_kernel(h, LBM_KERNEL_AUTO);
     if (rc != LBM_OK) return bail(rc);
     // partial sums: enough for any kernel form on this grid
-    const long long nblk = std::max((long long)((g.nx + 31) / 32) * g.ny * g.nz,
-                                    (long long)(g.nx / lbm::SEG) * g.ny * g.nz);
+    const long long nblk = std::max((long long)((g.nx + 31) / 32) * g.ny * g.nz, 8LL * g.ny * g.nz);
     rc = ensure_part(h, nblk * lbm::K_PART);
     if (rc != LBM_OK) return bail(rc);
     *out = h;

@@ -25,7 +25,10 @@ struct lbm_handle {
     int bx;                      // threads per block along x (one-cell / two-cell kernels)
     bool pair;                   // two cells per thread (even nx)
     int kernel;                  // LBM_KERNEL_* in use (never AUTO)
-    int tma_grid;                // CTAs of the warp-pipelined kernel
+    int tma_grid;                // CTAs of the row-pipelined kernel
+    int tma_warps;               // warps per CTA of the row-pipelined kernel (4 or 8)
+    int tma_stages;              // ring stages of the row-pipelined kernel
+    int tma_smem;                // dynamic shared memory bytes of the row-pipelined kernel
     int *err;                    // device flag set by a timed-out pipeline wait
     cudaGraphExec_t chunk[2];    // kGraphSteps plain steps starting from cur = 0 / 1
 };

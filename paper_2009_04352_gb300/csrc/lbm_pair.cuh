@@ -99,6 +99,8 @@ struct PairState {
 // and the update of the pair is  delta_a = de + dd,  delta_b = de - dd  with
 //   de = omega w (S0 + 9/2 rho (e.u)^2) - 3 w gk u.F + 9 w gk (e.u)(e.F) - omega s / 2
 //   dd = 3 omega w rho (e.u) + 3 w gk (e.F) - omega d / 2.
+// Only s and d are kept through the collision (the new populations are
+// (s' + d') / 2 and (s' - d') / 2), which keeps 18 fewer values live.
 __device__ __forceinline__ PairState collide_pair(float2 (&f)[Q], const Phys &p)
 {
     PairState c;
@@ -178,18 +180,21 @@ __device__ __forceinline__ PairState collide_pair(float2 (&f)[Q], const Phys &p)
         if (ex_of(a)) mx = ex_of(a) > 0 ? add2(mx, dd) : sub2(mx, dd);
         if (ey_of(a)) my = ey_of(a) > 0 ? add2(my, dd) : sub2(my, dd);
         if (ez_of(a)) mz = ez_of(a) > 0 ? add2(mz, dd) : sub2(mz, dd);
-        f[a] = add2(f[a], add2(de, dd));
-        f[a + 1] = add2(f[a + 1], sub2(de, dd));
+        // the pair's new sum and difference (delta_a = de + dd, delta_b = de - dd)
+        sk[k] = fma2(bc(2.f), de, sk[k]);
+        dk[k] = fma2(bc(2.f), dd, dk[k]);
     }
-    // exact momentum F and mass 0 of the update (see collide())
-    const float2 cx = sub2(bc(0.5f * p.Fx), mx), cy = sub2(bc(0.5f * p.Fy), my), cz = sub2(bc(0.5f * p.Fz), mz);
-    f[1] = add2(f[1], cx);
-    f[2] = sub2(f[2], cx);
-    f[3] = add2(f[3], cy);
-    f[4] = sub2(f[4], cy);
-    f[5] = add2(f[5], cz);
-    f[6] = sub2(f[6], cz);
+    // exact momentum F and mass 0 of the update (see collide()): the axis pairs
+    // take the momentum residual, the rest population the mass residual
+    dk[0] = fma2(bc(2.f), sub2(bc(0.5f * p.Fx), mx), dk[0]);
+    dk[1] = fma2(bc(2.f), sub2(bc(0.5f * p.Fy), my), dk[1]);
+    dk[2] = fma2(bc(2.f), sub2(bc(0.5f * p.Fz), mz), dk[2]);
     f[0] = fma2(bc(-2.f), mass, f[0]);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        f[2 * k + 1] = mul2(bc(0.5f), add2(sk[k], dk[k]));
+        f[2 * k + 2] = mul2(bc(0.5f), sub2(sk[k], dk[k]));
+    }
     return c;
 }
 

@@ -279,5 +279,7 @@ def test_kernel_selection_rules():
         ch.set_kernel(lbm.KERNEL_PAIR)
     ch.close()
     ch = lbm.Channel.from_case(case.with_(nx=128))
+    assert ch.kernel == lbm.KERNEL_PAIR
+    ch.set_kernel(lbm.KERNEL_TMA)
     assert ch.kernel == lbm.KERNEL_TMA
     ch.close()
