@@ -203,6 +203,64 @@ int lbm_conservation(lbm_handle *h, double *out);
  * on the shared array and must be ordered by the caller. */
 int lbm_plane_profile_noalloc(lbm_handle *h, double *out_dev);
 
+/* ---------------------------------------------------------------------------
+ * Batched ensemble: independent channels of uneven sizes and parameters
+ * advanced together by one persistent kernel launch per time step (plain
+ * steps replayed from a CUDA graph). Each member is the channel lbm_create
+ * would build from the same arguments; its populations live in one pool owned
+ * by the batch.
+ * ------------------------------------------------------------------------- */
+
+typedef struct {
+    lbm_grid grid;          /* nx even and >= 2 */
+    double tau;
+    double C_s;
+    double force[3];
+    lbm_wall_model wall;
+} lbm_member;
+
+typedef struct lbm_batch lbm_batch;
+
+/* Create n >= 1 members (at rest) in one population pool on the current
+ * device, all with the given storage precision, ordered on cuda_stream.
+ * Errors: LBM_ERR_ARG (a member's grid or parameters), LBM_ERR_OOM. */
+int lbm_batch_create(int n, const lbm_member *members, int precision, void *cuda_stream, lbm_batch **out);
+
+/* Member i as an lbm_handle view (NULL if out of range). Every call of the
+ * single-channel API that does not advance time works on it (initial field,
+ * populations in/out, moments, wall stress, plane statistics, conservation);
+ * lbm_step and lbm_set_kernel return LBM_ERR_STATE, lbm_destroy ignores it.
+ * The view stays valid until lbm_batch_destroy. */
+lbm_handle *lbm_batch_member(lbm_batch *b, int i);
+
+/* Total cells of all members. */
+long long lbm_batch_cells(lbm_batch *b);
+
+/* Plane statistics of every member at steps whose index is a multiple of
+ * `every` (0 = never), accumulated in each member's lbm_plane_stats. */
+int lbm_batch_set_stats_every(lbm_batch *b, int every);
+
+/* Advance every member by n steps: one launch of the persistent batch kernel
+ * per step over the work list of all members' tiles. Asynchronous. */
+int lbm_batch_step(lbm_batch *b, int n);
+
+/* Launch shape: threads per CTA (64 or 128; a tile is 2 * threads cells of one
+ * row) and CTAs per SM (<= 0 or above the occupancy limit selects the limit). */
+int lbm_batch_set_config(lbm_batch *b, int threads, int ctas_per_sm);
+int lbm_batch_get_config(lbm_batch *b, int *threads, int *ctas_per_sm, int *grid, long long *tiles);
+
+/* Time every launch shape for `steps` steps (after 2 warm-up steps) and keep
+ * the fastest; best_ms (nullable) receives its time per step. The timed steps
+ * advance all members like lbm_batch_step, so tune before initialising the
+ * members. Synchronises. */
+int lbm_batch_autotune(lbm_batch *b, int steps, double *best_ms);
+
+/* Block until the batch's work has finished. */
+int lbm_batch_sync(lbm_batch *b);
+
+/* Free the batch, its pool and its member views. NULL is ignored. */
+void lbm_batch_destroy(lbm_batch *b);
+
 /* Block until all work queued on the handle's stream has finished. Returns
  * LBM_ERR_CUDA if a wait inside the pipelined kernel timed out (the kernel then
  * stops early and leaves the step incomplete). */

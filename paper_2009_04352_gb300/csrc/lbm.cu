@@ -281,8 +281,10 @@ extern "C" {
 
 const char *lbm_last_error(void) { return g_err; }
 
-int lbm_create(lbm_grid g, double tau, double C_s, const double force[3], lbm_wall_model wm, int precision,
-               int layout, void *cuda_stream, lbm_handle **out)
+}  // extern "C"
+
+int lbm_create_handle(lbm_grid g, double tau, double C_s, const double force[3], lbm_wall_model wm, int precision,
+                      int layout, void *cuda_stream, void *pop0, void *pop1, lbm_handle **out)
 {
     if (!out) return fail(LBM_ERR_ARG, "out is NULL");
     *out = nullptr;
@@ -324,13 +326,18 @@ int lbm_create(lbm_grid g, double tau, double C_s, const double force[3], lbm_wa
     h->pair = (g.nx % 2) == 0;
 
     auto bail = [&](int rc) {
-        lbm_destroy(h);
+        lbm_free_handle(h);
         return rc;
     };
     if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess)
         return bail(fail(LBM_ERR_CUDA, "cannot create capture stream"));
     const size_t bytes = (size_t)lbm::Q * plane * elem_size(h);
-    for (int i = 0; i < 2; ++i) {
+    h->member = pop0 != nullptr;
+    if (h->member) {
+        h->f[0] = pop0;
+        h->f[1] = pop1;
+    }
+    for (int i = 0; i < 2 && !h->member; ++i) {
         if (cudaMalloc(&h->f[i], bytes) != cudaSuccess) {
             cudaGetLastError();
             return bail(fail(LBM_ERR_OOM, "cannot allocate %zu bytes of populations", bytes));
@@ -360,6 +367,30 @@ int lbm_create(lbm_grid g, double tau, double C_s, const double force[3], lbm_wa
     if (rc != LBM_OK) return bail(rc);
     *out = h;
     return LBM_OK;
+}
+
+void lbm_free_handle(lbm_handle *h)
+{
+    if (!h) return;
+    if (h->stream || h->f[0]) cudaStreamSynchronize(h->stream);
+    for (int i = 0; i < 2; ++i) {
+        if (h->chunk[i]) cudaGraphExecDestroy(h->chunk[i]);
+        if (h->f[i] && !h->member) cudaFree(h->f[i]);
+    }
+    if (h->part) cudaFree(h->part);
+    if (h->tw) cudaFree(h->tw);
+    if (h->acc) cudaFree(h->acc);
+    if (h->err) cudaFree(h->err);
+    if (h->cap) cudaStreamDestroy(h->cap);
+    delete h;
+}
+
+extern "C" {
+
+int lbm_create(lbm_grid g, double tau, double C_s, const double force[3], lbm_wall_model wm, int precision,
+               int layout, void *cuda_stream, lbm_handle **out)
+{
+    return lbm_create_handle(g, tau, C_s, force, wm, precision, layout, cuda_stream, nullptr, nullptr, out);
 }
 
 int lbm_init_channel(lbm_handle *h, const double *u_mean_x, double noise_amp, uint64_t seed)
@@ -426,6 +457,7 @@ int lbm_set_stats_every(lbm_handle *h, int every)
 int lbm_step(lbm_handle *h, int n)
 {
     if (!h || n < 0) return fail(LBM_ERR_ARG, "invalid argument");
+    if (h->member) return fail(LBM_ERR_STATE, "a batch member is advanced by lbm_batch_step");
     while (n > 0) {
         const bool sample = h->stats_every > 0 && (h->step % h->stats_every) == 0;
         if (sample) {
@@ -469,6 +501,7 @@ long long lbm_get_step(lbm_handle *h) { return h ? h->step : -1; }
 int lbm_set_kernel(lbm_handle *h, int kernel)
 {
     if (!h) return fail(LBM_ERR_ARG, "NULL handle");
+    if (h->member) return fail(LBM_ERR_STATE, "a batch member runs the batch kernel");
     CK(cudaStreamSynchronize(h->stream));
     return select_kernel(h, kernel);
 }
@@ -551,18 +584,8 @@ int lbm_sync(lbm_handle *h)
 
 void lbm_destroy(lbm_handle *h)
 {
-    if (!h) return;
-    if (h->stream || h->f[0]) cudaStreamSynchronize(h->stream);
-    for (int i = 0; i < 2; ++i) {
-        if (h->chunk[i]) cudaGraphExecDestroy(h->chunk[i]);
-        if (h->f[i]) cudaFree(h->f[i]);
-    }
-    if (h->part) cudaFree(h->part);
-    if (h->tw) cudaFree(h->tw);
-    if (h->acc) cudaFree(h->acc);
-    if (h->err) cudaFree(h->err);
-    if (h->cap) cudaStreamDestroy(h->cap);
-    delete h;
+    if (!h || h->member) return;   // members are freed with their batch
+    lbm_free_handle(h);
 }
 
 }  // extern "C"

@@ -1,0 +1,433 @@
+// Batched ensemble: many independent channels of uneven sizes and parameters
+// advanced by ONE persistent kernel launch per time step.
+//
+// All members' lattices live in one device pool. The work list is the
+// concatenation of every member's tiles (a tile = 2 * threads consecutive
+// cells of one (y, z) row, the unit of the two-cell kernel); member i owns
+// tiles [tile0_i, tile0_i + tiles_i). A grid of CTAs sized to the GPU
+// (CTAs per SM x SM count) walks the list with a stride of the grid size;
+// each tile finds its member by binary search over tile0, stages the member's
+// descriptor (geometry, physics, pool offsets) in shared memory and runs the
+// same tile code as the single-channel kernel. Plain steps are replayed from a
+// CUDA graph of 16 steps; sampled steps add one plane reduction per member.
+// The launch shape (threads per CTA, CTAs per SM) is chosen by a timing
+// autotuner.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_handle.h"
+#include "lbm_pair.cuh"
+
+namespace {
+
+constexpr int kBatchGraphSteps = 16;
+
+struct BatchInst {
+    lbm::Geom g;
+    lbm::Phys p;
+    long long off[2];   // element offsets of the member's two lattices in the pool
+    float *tw;          // member's wall-stress plane
+    double *part;       // member's block partials
+    long long tile0;    // first tile of the member
+    int nxb;            // tiles per row
+};
+
+template <typename T, bool STATS>
+__global__ void __launch_bounds__(128) k_batch_step(const BatchInst *__restrict__ inst, int n, long long total,
+                                                    T *__restrict__ pool, int cur)
+{
+    __shared__ BatchInst s;
+    __shared__ int s_member;
+    if (threadIdx.x == 0) s_member = -1;
+    for (long long t = blockIdx.x; t < total; t += gridDim.x) {
+        __syncthreads();   // every thread is done with the previous descriptor
+        if (threadIdx.x == 0) {
+            int lo = 0, hi = n - 1;   // last member whose first tile is <= t
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (inst[mid].tile0 <= t)
+                    lo = mid;
+                else
+                    hi = mid - 1;
+            }
+            if (lo != s_member) {
+                s = inst[lo];
+                s_member = lo;
+            }
+        }
+        __syncthreads();
+        const long long local = t - s.tile0;
+        const int xb = (int)(local % s.nxb);
+        const long long row = local / s.nxb;
+        const int y = (int)(row % s.g.ny), z = (int)(row / s.g.ny);
+        double *part = STATS ? s.part + (((long long)y * s.g.nz + z) * s.nxb + xb) * lbm::K_PART : nullptr;
+        lbm::pair_tile<T, STATS>(pool + s.off[cur], pool + s.off[cur ^ 1], s.g, s.p, s.tw, part, xb, y, z);
+    }
+}
+
+int fail(int code, const char *msg) { return lbm_record_error(code, msg); }
+
+int fail_cuda(cudaError_t e, const char *what)
+{
+    char buf[256];
+    snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
+    return lbm_record_error(LBM_ERR_CUDA, buf);
+}
+
+#define BK(call)                                        \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return fail_cuda(e_, #call); \
+    } while (0)
+
+}  // namespace
+
+struct lbm_batch {
+    int n;
+    int precision;
+    cudaStream_t stream;
+    cudaStream_t cap;
+    std::vector<lbm_handle *> members;
+    void *pool;
+    std::vector<long long> off;   // per member: offset of lattice 0 (lattice 1 follows)
+    BatchInst *d_inst;
+    long long tiles;
+    int threads;                  // threads per CTA (tile = 2 * threads cells)
+    int ctas_per_sm;
+    int grid;
+    int sms;
+    int cur;
+    long long step;
+    int stats_every;
+    cudaGraphExec_t chunk[2];
+};
+
+namespace {
+
+size_t elem_bytes(int precision) { return precision == LBM_FP16_SHIFTED ? 2 : 4; }
+
+void drop_graphs(lbm_batch *b)
+{
+    for (int i = 0; i < 2; ++i)
+        if (b->chunk[i]) {
+            cudaGraphExecDestroy(b->chunk[i]);
+            b->chunk[i] = nullptr;
+        }
+}
+
+int max_ctas_per_sm(const lbm_batch *b, int threads, int *out)
+{
+    int per_sm = 0, st = 0;
+    if (b->precision == LBM_FP16_SHIFTED) {
+        BK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_step<__half, false>, threads, 0));
+        BK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&st, k_batch_step<__half, true>, threads, 0));
+    } else {
+        BK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_step<float, false>, threads, 0));
+        BK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&st, k_batch_step<float, true>, threads, 0));
+    }
+    *out = std::min(per_sm, st);
+    return LBM_OK;
+}
+
+// Rebuild the descriptor table for `threads` per CTA and size the grid.
+int configure(lbm_batch *b, int threads, int ctas_per_sm)
+{
+    if (threads != 64 && threads != 128) return fail(LBM_ERR_ARG, "threads per CTA must be 64 or 128");
+    int max_per_sm = 0;
+    int rc = max_ctas_per_sm(b, threads, &max_per_sm);
+    if (rc != LBM_OK) return rc;
+    if (ctas_per_sm <= 0 || ctas_per_sm > max_per_sm) ctas_per_sm = max_per_sm;
+    std::vector<BatchInst> h(b->n);
+    long long tile = 0;
+    for (int i = 0; i < b->n; ++i) {
+        const lbm_handle *m = b->members[i];
+        BatchInst &d = h[i];
+        memset(&d, 0, sizeof(d));
+        d.g = m->g;
+        d.p = m->p;
+        d.off[0] = b->off[i];
+        d.off[1] = b->off[i] + (long long)lbm::Q * m->g.plane;
+        d.tw = m->tw;
+        d.part = m->part;
+        d.nxb = (m->g.nx / 2 + threads - 1) / threads;
+        d.tile0 = tile;
+        tile += (long long)d.nxb * m->g.ny * m->g.nz;
+    }
+    BK(cudaStreamSynchronize(b->stream));
+    BK(cudaMemcpy(b->d_inst, h.data(), sizeof(BatchInst) * b->n, cudaMemcpyHostToDevice));
+    b->tiles = tile;
+    b->threads = threads;
+    b->ctas_per_sm = ctas_per_sm;
+    b->grid = (int)std::min<long long>((long long)b->sms * ctas_per_sm, tile);
+    drop_graphs(b);
+    return LBM_OK;
+}
+
+int launch(lbm_batch *b, cudaStream_t s, int cur, bool stats)
+{
+    const dim3 grid(b->grid), block(b->threads);
+    if (b->precision == LBM_FP16_SHIFTED) {
+        __half *pool = (__half *)b->pool;
+        if (stats)
+            k_batch_step<__half, true><<<grid, block, 0, s>>>(b->d_inst, b->n, b->tiles, pool, cur);
+        else
+            k_batch_step<__half, false><<<grid, block, 0, s>>>(b->d_inst, b->n, b->tiles, pool, cur);
+    } else {
+        float *pool = (float *)b->pool;
+        if (stats)
+            k_batch_step<float, true><<<grid, block, 0, s>>>(b->d_inst, b->n, b->tiles, pool, cur);
+        else
+            k_batch_step<float, false><<<grid, block, 0, s>>>(b->d_inst, b->n, b->tiles, pool, cur);
+    }
+    BK(cudaGetLastError());
+    if (stats) {
+        for (int i = 0; i < b->n; ++i) {
+            lbm_handle *m = b->members[i];
+            const long long per_plane = (long long)((m->g.nx / 2 + b->threads - 1) / b->threads) * m->g.nz;
+            lbm::k_reduce_planes<<<m->g.ny, 256, 0, s>>>(m->part, per_plane, m->g.ny, m->acc,
+                                                         m->acc + (long long)m->g.ny * lbm::K_STATS);
+        }
+        BK(cudaGetLastError());
+    }
+    return LBM_OK;
+}
+
+int build_chunk(lbm_batch *b, int start)
+{
+    cudaGraph_t graph = nullptr;
+    BK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+    int rc = LBM_OK;
+    for (int i = 0; i < kBatchGraphSteps && rc == LBM_OK; ++i) rc = launch(b, b->cap, start ^ (i & 1), false);
+    cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
+    if (rc != LBM_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess) return fail_cuda(e, "graph capture");
+    e = cudaGraphInstantiate(&b->chunk[start], graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail_cuda(e, "graph instantiate");
+    return LBM_OK;
+}
+
+void sync_members(lbm_batch *b)
+{
+    for (lbm_handle *m : b->members) {
+        m->cur = b->cur;
+        m->step = b->step;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_batch_create(int n, const lbm_member *members, int precision, void *cuda_stream, lbm_batch **out)
+{
+    if (!out) return fail(LBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || !members) return fail(LBM_ERR_ARG, "a batch needs n >= 1 members");
+    if (precision != LBM_FP32 && precision != LBM_FP16_SHIFTED) return fail(LBM_ERR_ARG, "unknown precision");
+    for (int i = 0; i < n; ++i)
+        if (members[i].grid.nx < 2 || members[i].grid.nx % 2)
+            return fail(LBM_ERR_ARG, "batch members need an even nx >= 2");
+    lbm_batch *b = new lbm_batch();
+    b->n = n;
+    b->precision = precision;
+    b->stream = (cudaStream_t)cuda_stream;
+    b->chunk[0] = b->chunk[1] = nullptr;
+    b->pool = nullptr;
+    b->d_inst = nullptr;
+    b->cap = nullptr;
+    auto bail = [&](int rc) {
+        lbm_batch_destroy(b);
+        return rc;
+    };
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return bail(fail(LBM_ERR_CUDA, "cannot query the device"));
+    if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(fail(LBM_ERR_CUDA, "cannot create capture stream"));
+    // pool layout: per member two lattices of 19 row-padded planes, 256-byte aligned
+    const size_t eb = elem_bytes(precision);
+    long long total = 0;
+    for (int i = 0; i < n; ++i) {
+        const lbm_grid &g = members[i].grid;
+        const long long sx = (g.nx + 31) / 32 * 32;
+        const long long plane = sx * g.ny * g.nz;
+        if (plane > 2147483647LL) return bail(fail(LBM_ERR_ARG, "a member grid is too large"));
+        b->off.push_back(total);
+        total += 2LL * lbm::Q * plane;
+        total = (total * (long long)eb + 255) / 256 * 256 / (long long)eb;
+    }
+    if (cudaMalloc(&b->pool, (size_t)total * eb) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(LBM_ERR_OOM, "cannot allocate the batch population pool"));
+    }
+    if (cudaMemsetAsync(b->pool, 0, (size_t)total * eb, b->stream) != cudaSuccess)
+        return bail(fail(LBM_ERR_CUDA, "memset failed"));
+    for (int i = 0; i < n; ++i) {
+        const lbm_member &m = members[i];
+        char *base = (char *)b->pool + (size_t)b->off[i] * eb;
+        const long long sx = (m.grid.nx + 31) / 32 * 32;
+        char *second = base + (size_t)lbm::Q * sx * m.grid.ny * m.grid.nz * eb;
+        lbm_handle *h = nullptr;
+        const int rc = lbm_create_handle(m.grid, m.tau, m.C_s, m.force, m.wall, precision, LBM_PULL2, cuda_stream, base,
+                                         second, &h);
+        if (rc != LBM_OK) return bail(rc);
+        b->members.push_back(h);
+    }
+    if (cudaMalloc((void **)&b->d_inst, sizeof(BatchInst) * n) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(LBM_ERR_OOM, "cannot allocate the batch descriptors"));
+    }
+    b->cur = 0;
+    b->step = 0;
+    b->stats_every = 0;
+    const int rc = configure(b, 128, 0);
+    if (rc != LBM_OK) return bail(rc);
+    *out = b;
+    return LBM_OK;
+}
+
+lbm_handle *lbm_batch_member(lbm_batch *b, int i)
+{
+    if (!b || i < 0 || i >= b->n) return nullptr;
+    return b->members[i];
+}
+
+long long lbm_batch_cells(lbm_batch *b)
+{
+    if (!b) return -1;
+    long long c = 0;
+    for (const lbm_handle *m : b->members) c += (long long)m->g.nx * m->g.ny * m->g.nz;
+    return c;
+}
+
+int lbm_batch_set_stats_every(lbm_batch *b, int every)
+{
+    if (!b || every < 0) return fail(LBM_ERR_ARG, "invalid argument");
+    b->stats_every = every;
+    return LBM_OK;
+}
+
+int lbm_batch_step(lbm_batch *b, int n)
+{
+    if (!b || n < 0) return fail(LBM_ERR_ARG, "invalid argument");
+    while (n > 0) {
+        const bool sample = b->stats_every > 0 && (b->step % b->stats_every) == 0;
+        if (sample) {
+            const int rc = launch(b, b->stream, b->cur, true);
+            if (rc != LBM_OK) return rc;
+            for (lbm_handle *m : b->members) m->nsamples += 1;
+            b->cur ^= 1;
+            b->step += 1;
+            n -= 1;
+            continue;
+        }
+        long long run = n;
+        if (b->stats_every > 0) run = std::min<long long>(run, b->stats_every - (b->step % b->stats_every));
+        while (run >= kBatchGraphSteps) {
+            if (!b->chunk[b->cur]) {
+                const int rc = build_chunk(b, b->cur);
+                if (rc != LBM_OK) return rc;
+            }
+            BK(cudaGraphLaunch(b->chunk[b->cur], b->stream));
+            b->step += kBatchGraphSteps;
+            run -= kBatchGraphSteps;
+            n -= kBatchGraphSteps;
+        }
+        while (run > 0) {
+            const int rc = launch(b, b->stream, b->cur, false);
+            if (rc != LBM_OK) return rc;
+            b->cur ^= 1;
+            b->step += 1;
+            run -= 1;
+            n -= 1;
+        }
+    }
+    sync_members(b);
+    return LBM_OK;
+}
+
+int lbm_batch_set_config(lbm_batch *b, int threads, int ctas_per_sm)
+{
+    if (!b) return fail(LBM_ERR_ARG, "NULL batch");
+    return configure(b, threads, ctas_per_sm);
+}
+
+int lbm_batch_get_config(lbm_batch *b, int *threads, int *ctas_per_sm, int *grid, long long *tiles)
+{
+    if (!b) return fail(LBM_ERR_ARG, "NULL batch");
+    if (threads) *threads = b->threads;
+    if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm;
+    if (grid) *grid = b->grid;
+    if (tiles) *tiles = b->tiles;
+    return LBM_OK;
+}
+
+int lbm_batch_autotune(lbm_batch *b, int steps, double *best_ms)
+{
+    if (!b || steps < 1) return fail(LBM_ERR_ARG, "invalid argument");
+    cudaEvent_t e0, e1;
+    BK(cudaEventCreate(&e0));
+    BK(cudaEventCreate(&e1));
+    double best = 1e300;
+    int best_t = 128, best_c = 0;
+    const int saved_stats = b->stats_every;
+    b->stats_every = 0;
+    for (int threads : {64, 128}) {
+        int max_per_sm = 0;
+        int rc = max_ctas_per_sm(b, threads, &max_per_sm);
+        if (rc != LBM_OK) return rc;
+        for (int c = std::max(1, max_per_sm / 4); c <= max_per_sm; c += std::max(1, max_per_sm / 4)) {
+            rc = configure(b, threads, c);
+            if (rc == LBM_OK) rc = lbm_batch_step(b, 2);   // warm-up
+            if (rc != LBM_OK) return rc;
+            BK(cudaEventRecord(e0, b->stream));
+            rc = lbm_batch_step(b, steps);
+            if (rc != LBM_OK) return rc;
+            BK(cudaEventRecord(e1, b->stream));
+            BK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            BK(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) {
+                best = ms;
+                best_t = threads;
+                best_c = c;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->stats_every = saved_stats;
+    if (best_ms) *best_ms = best / steps;
+    return configure(b, best_t, best_c);
+}
+
+int lbm_batch_sync(lbm_batch *b)
+{
+    if (!b) return fail(LBM_ERR_ARG, "NULL batch");
+    BK(cudaStreamSynchronize(b->stream));
+    return LBM_OK;
+}
+
+void lbm_batch_destroy(lbm_batch *b)
+{
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    drop_graphs(b);
+    for (lbm_handle *m : b->members) lbm_free_handle(m);
+    if (b->d_inst) cudaFree(b->d_inst);
+    if (b->pool) cudaFree(b->pool);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    delete b;
+}
+
+}  // extern "C"

@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include "lbm.h"
 #include "lbm_device.cuh"
 
 struct lbm_handle {
@@ -31,7 +32,16 @@ struct lbm_handle {
     int tma_smem;                // dynamic shared memory bytes of the row-pipelined kernel
     int *err;                    // device flag set by a timed-out pipeline wait
     cudaGraphExec_t chunk[2];    // kGraphSteps plain steps starting from cur = 0 / 1
+    bool member;                 // member view of a batch: populations owned by the batch
 };
+
+// Create a handle; with pop0/pop1 non-NULL it is a member view whose two
+// lattices live in a batch pool (nothing is allocated for them).
+int lbm_create_handle(lbm_grid g, double tau, double C_s, const double force[3], lbm_wall_model wm, int precision,
+                      int layout, void *cuda_stream, void *pop0, void *pop1, lbm_handle **out);
+
+// Free a handle, member views included.
+void lbm_free_handle(lbm_handle *h);
 
 // Record an error message for lbm_last_error() and return `code`.
 int lbm_record_error(int code, const char *msg);

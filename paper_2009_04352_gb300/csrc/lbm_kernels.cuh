@@ -174,6 +174,7 @@ __device__ __forceinline__ void block_reduce_store(double (&v)[N], double *__res
         for (int w = 0; w < nw; ++w) s += red[w][threadIdx.x];
         out[threadIdx.x] = s;
     }
+    __syncthreads();   // red[] may be reused by the next call in the same block
 }
 
 // One time step, two lattices: gather from src (streaming + wall reflection),

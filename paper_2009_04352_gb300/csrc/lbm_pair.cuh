@@ -198,13 +198,16 @@ __device__ __forceinline__ PairState collide_pair(float2 (&f)[Q], const Phys &p)
     return c;
 }
 
+// One tile: the x-pairs xb * blockDim.x + threadIdx.x of row (y, z), i.e.
+// cells [2 xb blockDim.x, 2 (xb + 1) blockDim.x). With STATS the block writes
+// its FP64 partial sums to part_blk[0..K_PART).
 template <typename T, bool STATS>
-__global__ void __launch_bounds__(128) k_step_pair(const T *__restrict__ src, T *__restrict__ dst, Geom g, Phys p,
-                                                   float *__restrict__ tw_out, double *__restrict__ part)
+__device__ __forceinline__ void pair_tile(const T *__restrict__ src, T *__restrict__ dst, const Geom &g, const Phys &p,
+                                          float *__restrict__ tw_out, double *__restrict__ part_blk, int xb, int y,
+                                          int z)
 {
     const int lane = threadIdx.x & 31;
-    const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-    const int y = blockIdx.y, z = blockIdx.z;
+    const int x0 = 2 * (xb * blockDim.x + threadIdx.x);
     const bool valid = x0 < g.nx;
     const int xl = valid ? x0 : g.nx - 2;   // lanes past the row end read in bounds and store nothing
     const int zm = z == 0 ? g.nz - 1 : z - 1, zp = z == g.nz - 1 ? 0 : z + 1;
@@ -271,9 +274,17 @@ __global__ void __launch_bounds__(128) k_step_pair(const T *__restrict__ src, T 
                 v[14] += m2;
             }
         }
-        const long long blk = ((long long)y * g.nz + z) * gridDim.x + blockIdx.x;
-        block_reduce_store<K_PART>(v, part + blk * K_PART);
+        block_reduce_store<K_PART>(v, part_blk);
     }
+}
+
+template <typename T, bool STATS>
+__global__ void __launch_bounds__(128) k_step_pair(const T *__restrict__ src, T *__restrict__ dst, Geom g, Phys p,
+                                                   float *__restrict__ tw_out, double *__restrict__ part)
+{
+    const int y = blockIdx.y, z = blockIdx.z;
+    const long long blk = ((long long)y * g.nz + z) * gridDim.x + blockIdx.x;
+    pair_tile<T, STATS>(src, dst, g, p, tw_out, STATS ? part + blk * K_PART : nullptr, blockIdx.x, y, z);
 }
 
 }  // namespace lbm

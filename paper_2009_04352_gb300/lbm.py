@@ -48,6 +48,11 @@ class lbm_wall_model(C.Structure):
                 ("nu", C.c_double), ("newton_iters", C.c_int)]
 
 
+class lbm_member(C.Structure):
+    _fields_ = [("grid", lbm_grid), ("tau", C.c_double), ("C_s", C.c_double), ("force", C.c_double * 3),
+                ("wall", lbm_wall_model)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -72,6 +77,17 @@ _SIGNATURES = {
     "lbm_conservation": (C.c_int, [_VP, _DP]),
     "lbm_plane_profile_noalloc": (C.c_int, [_VP, _VP]),
     "lbm_sync": (C.c_int, [_VP]),
+    "lbm_batch_create": (C.c_int, [C.c_int, C.POINTER(lbm_member), C.c_int, _VP, C.POINTER(_VP)]),
+    "lbm_batch_member": (_VP, [_VP, C.c_int]),
+    "lbm_batch_cells": (C.c_longlong, [_VP]),
+    "lbm_batch_set_stats_every": (C.c_int, [_VP, C.c_int]),
+    "lbm_batch_step": (C.c_int, [_VP, C.c_int]),
+    "lbm_batch_set_config": (C.c_int, [_VP, C.c_int, C.c_int]),
+    "lbm_batch_get_config": (C.c_int, [_VP, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                       C.POINTER(C.c_longlong)]),
+    "lbm_batch_autotune": (C.c_int, [_VP, C.c_int, _DP]),
+    "lbm_batch_sync": (C.c_int, [_VP]),
+    "lbm_batch_destroy": (None, [_VP]),
     "lbm_destroy": (None, [_VP]),
     "lbm_last_error": (C.c_char_p, []),
 }
@@ -291,3 +307,87 @@ class Channel:
 
     def sync(self):
         lbm_sync(self._h)
+
+
+# ------------------------------------------------------------ batched ensemble
+
+def member_of(case):
+    m = lbm_member()
+    m.grid = lbm_grid(case.nx, case.ny, case.nz)
+    m.tau = case.tau
+    m.C_s = case.cs
+    for i in range(3):
+        m.force[i] = case.force[i]
+    m.wall = lbm_wall_model(case.wall, case.kappa, case.b_const, case.y1, case.nu_wall, case.newton_iters)
+    return m
+
+
+class _MemberView(Channel):
+    """A batch member seen through the single-channel API (owned by the batch)."""
+
+    def __init__(self, handle, case, precision):
+        self.nx, self.ny, self.nz = case.nx, case.ny, case.nz
+        self.n = self.nx * self.ny * self.nz
+        self.precision = precision
+        self._h = handle
+
+    def close(self):
+        self._h = None
+
+
+class Batch:
+    """Ensemble of independent channels advanced by one launch per step."""
+
+    def __init__(self, cases, precision=FP32, stream=None):
+        arr = (lbm_member * len(cases))(*[member_of(c) for c in cases])
+        out = C.c_void_p()
+        s = _current_stream() if stream is None else C.c_void_p(stream)
+        _check(lib().lbm_batch_create(len(cases), arr, int(precision), s, C.byref(out)))
+        self._b = out
+        self.cases = list(cases)
+        self.precision = precision
+        self.members = [_MemberView(C.c_void_p(lib().lbm_batch_member(out, i)), c, precision)
+                        for i, c in enumerate(cases)]
+
+    @property
+    def handle(self):
+        return self._b
+
+    @property
+    def cells(self):
+        return int(lib().lbm_batch_cells(self._b))
+
+    def set_stats_every(self, every):
+        _check(lib().lbm_batch_set_stats_every(self._b, int(every)))
+
+    def step(self, n=1):
+        _check(lib().lbm_batch_step(self._b, int(n)))
+
+    def set_config(self, threads, ctas_per_sm):
+        _check(lib().lbm_batch_set_config(self._b, int(threads), int(ctas_per_sm)))
+
+    def config(self):
+        t, c, g, tl = C.c_int(), C.c_int(), C.c_int(), C.c_longlong()
+        _check(lib().lbm_batch_get_config(self._b, C.byref(t), C.byref(c), C.byref(g), C.byref(tl)))
+        return {"threads": t.value, "ctas_per_sm": c.value, "grid": g.value, "tiles": tl.value}
+
+    def autotune(self, steps=5):
+        ms = C.c_double()
+        _check(lib().lbm_batch_autotune(self._b, int(steps), C.byref(ms)))
+        return ms.value
+
+    def sync(self):
+        _check(lib().lbm_batch_sync(self._b))
+
+    def close(self):
+        if self._b:
+            for m in self.members:
+                m.close()
+            lib().lbm_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
