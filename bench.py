@@ -150,6 +150,38 @@ def time_channel(case, precision, steps, warmup, stream, clocks=None):
     return ms, finite
 
 
+def time_batch(precision, steps, stream, peak):
+    """The 64-channel ensemble (uneven sizes and Re_tau), one launch per step,
+    launch shape from the autotuner."""
+    import torch
+    from paper_2009_04352_gb300 import autotune, lbm
+
+    cases = workload.batch_cases(64, seed=5)
+    with torch.cuda.stream(stream):
+        b = lbm.Batch(cases, precision=precision, stream=stream.cuda_stream)
+        tuned = autotune.tune_batch(b, steps=3)
+        for m, c in zip(b.members, cases):
+            m.init_channel(workload.u_mean_profile(c), workload.noise_amplitude(c), c.seed)
+        b.step(5)
+        b.sync()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        b.step(steps)
+        ev1.record(stream)
+        ev1.synchronize()
+        ms = ev0.elapsed_time(ev1) / steps
+        finite = all(bool(np.all(np.isfinite(m.conservation()))) for m in b.members[:4])
+        cells = b.cells
+        cfg = b.config()
+        b.close()
+    gbs = BYTES_PER_LUP[precision] * cells / (ms * 1e-3) / 1e9
+    return {"workload": "64 channels, ny in {32,48,64,96,128}, nx=4ny, nz=2ny, Re_tau in {180..2003}",
+            "cells": cells, "MLUPS": cells / (ms * 1e-3) / 1e6, "ms_per_step": ms, "GBs": gbs, "frac": gbs / peak,
+            "finite": finite, "launch": {"threads": cfg["threads"], "ctas_per_sm": cfg["ctas_per_sm"],
+                                         "grid": cfg["grid"], "tiles": cfg["tiles"],
+                                         "from_cache": tuned["cached"]}}
+
+
 class _Null:
     def __enter__(self):
         return self
@@ -311,6 +343,9 @@ def main():
                        "plane statistics every 10 steps, moments and statistics read back"}
 
     variants = {}
+    if not args.no_variants and rank == 0:
+        for name, prec in (("c5_batch64_fp32", lbm.FP32), ("c5_batch64_fp16", lbm.FP16_SHIFTED)):
+            variants[name] = time_batch(prec, 30, stream, peak)
     if not args.no_variants and rank == 0:
         for name, wl, prec, steps in (("c3_fp32", "c3", lbm.FP32, 2000), ("c3_fp16", "c3", lbm.FP16_SHIFTED, 2000),
                                       ("c4_fp32", "c4", lbm.FP32, 300), ("c4_fp16", "c4", lbm.FP16_SHIFTED, 300)):

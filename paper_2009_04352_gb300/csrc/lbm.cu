@@ -181,6 +181,23 @@ int configure_rows(lbm_handle *h)
     return rc;
 }
 
+// Two-cell step launched with programmatic stream serialisation (see pdl_begin).
+template <typename T, bool STATS>
+cudaError_t launch_pair_pdl(lbm_handle *h, cudaStream_t s, dim3 grid, dim3 block, const void *a, void *b)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, lbm::k_step_pair<T, STATS>, (const T *)a, (T *)b, h->g, h->p, h->tw, h->part);
+}
+
 int launch_step(lbm_handle *h, cudaStream_t s, int src, bool stats)
 {
     const dim3 grid = step_grid(h), block(h->bx);
@@ -188,19 +205,15 @@ int launch_step(lbm_handle *h, cudaStream_t s, int src, bool stats)
     void *b = h->f[src ^ 1];
     if (h->kernel == LBM_KERNEL_TMA) {
         launch_tma(h, s, src, stats);
-    } else if (h->kernel == LBM_KERNEL_PAIR && h->precision == LBM_FP16_SHIFTED) {
-        if (stats)
-            lbm::k_step_pair<__half, true><<<grid, block, 0, s>>>((const __half *)a, (__half *)b, h->g, h->p, h->tw,
-                                                                  h->part);
-        else
-            lbm::k_step_pair<__half, false><<<grid, block, 0, s>>>((const __half *)a, (__half *)b, h->g, h->p, h->tw,
-                                                                   h->part);
     } else if (h->kernel == LBM_KERNEL_PAIR) {
-        if (stats)
-            lbm::k_step_pair<float, true><<<grid, block, 0, s>>>((const float *)a, (float *)b, h->g, h->p, h->tw, h->part);
+        cudaError_t e;
+        if (h->precision == LBM_FP16_SHIFTED)
+            e = stats ? launch_pair_pdl<__half, true>(h, s, grid, block, a, b)
+                      : launch_pair_pdl<__half, false>(h, s, grid, block, a, b);
         else
-            lbm::k_step_pair<float, false><<<grid, block, 0, s>>>((const float *)a, (float *)b, h->g, h->p, h->tw,
-                                                                  h->part);
+            e = stats ? launch_pair_pdl<float, true>(h, s, grid, block, a, b)
+                      : launch_pair_pdl<float, false>(h, s, grid, block, a, b);
+        if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "step launch: %s", cudaGetErrorString(e));
     } else if (h->precision == LBM_FP16_SHIFTED) {
         if (stats)
             lbm::k_step<__half, true><<<grid, block, 0, s>>>((const __half *)a, (__half *)b, h->g, h->p, h->tw, h->part);

@@ -5,10 +5,11 @@
 // concatenation of every member's tiles (a tile = 2 * threads consecutive
 // cells of one (y, z) row, the unit of the two-cell kernel); member i owns
 // tiles [tile0_i, tile0_i + tiles_i). A grid of CTAs sized to the GPU
-// (CTAs per SM x SM count) walks the list with a stride of the grid size;
-// each tile finds its member by binary search over tile0, stages the member's
-// descriptor (geometry, physics, pool offsets) in shared memory and runs the
-// same tile code as the single-channel kernel. Plain steps are replayed from a
+// (CTAs per SM x SM count) splits the list into contiguous shares; a CTA finds
+// the member of its first tile by binary search over tile0, stages the
+// member's descriptor (geometry, physics, pool offsets) in shared memory, and
+// then advances (tile, row, member) incrementally, running the same tile code
+// as the single-channel kernel. Plain steps are replayed from a
 // CUDA graph of 16 steps; sampled steps add one plane reduction per member.
 // The launch shape (threads per CTA, CTAs per SM) is chosen by a timing
 // autotuner.
@@ -38,35 +39,55 @@ struct BatchInst {
 };
 
 template <typename T, bool STATS>
-__global__ void __launch_bounds__(128) k_batch_step(const BatchInst *__restrict__ inst, int n, long long total,
+__global__ void __launch_bounds__(128, 5) k_batch_step(const BatchInst *__restrict__ inst, int n, long long total,
                                                     T *__restrict__ pool, int cur)
 {
+    lbm::pdl_begin();
+    // this CTA's contiguous share [t, t1) of the work list
+    const long long per = (total + gridDim.x - 1) / gridDim.x;
+    long long t = (long long)blockIdx.x * per;
+    const long long t1 = t + per < total ? t + per : total;
+    if (t >= t1) return;
     __shared__ BatchInst s;
-    __shared__ int s_member;
-    if (threadIdx.x == 0) s_member = -1;
-    for (long long t = blockIdx.x; t < total; t += gridDim.x) {
-        __syncthreads();   // every thread is done with the previous descriptor
-        if (threadIdx.x == 0) {
-            int lo = 0, hi = n - 1;   // last member whose first tile is <= t
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (inst[mid].tile0 <= t)
-                    lo = mid;
-                else
-                    hi = mid - 1;
-            }
-            if (lo != s_member) {
-                s = inst[lo];
-                s_member = lo;
-            }
+    int m = 0;   // last member whose first tile is <= t
+    {
+        int hi = n - 1;
+        while (m < hi) {
+            const int mid = (m + hi + 1) >> 1;
+            if (inst[mid].tile0 <= t)
+                m = mid;
+            else
+                hi = mid - 1;
         }
-        __syncthreads();
+    }
+    if (threadIdx.x == 0) s = inst[m];
+    __syncthreads();
+    // position of tile t inside member m, then advanced tile by tile
+    int xb, y, z;
+    {
         const long long local = t - s.tile0;
-        const int xb = (int)(local % s.nxb);
+        xb = (int)(local % s.nxb);
         const long long row = local / s.nxb;
-        const int y = (int)(row % s.g.ny), z = (int)(row / s.g.ny);
+        y = (int)(row % s.g.ny);
+        z = (int)(row / s.g.ny);
+    }
+    for (;;) {
         double *part = STATS ? s.part + (((long long)y * s.g.nz + z) * s.nxb + xb) * lbm::K_PART : nullptr;
         lbm::pair_tile<T, STATS>(pool + s.off[cur], pool + s.off[cur ^ 1], s.g, s.p, s.tw, part, xb, y, z);
+        if (++t >= t1) break;
+        if (++xb == s.nxb) {
+            xb = 0;
+            if (++y == s.g.ny) {
+                y = 0;
+                if (++z == s.g.nz) {
+                    z = 0;
+                    ++m;   // next member: every thread reaches this point together
+                    __syncthreads();
+                    if (threadIdx.x == 0) s = inst[m];
+                    __syncthreads();
+                }
+            }
+        }
     }
 }
 
@@ -168,23 +189,31 @@ int configure(lbm_batch *b, int threads, int ctas_per_sm)
     return LBM_OK;
 }
 
+template <typename T, bool STATS>
+cudaError_t launch_pdl(lbm_batch *b, cudaStream_t s, int cur)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(b->grid);
+    cfg.blockDim = dim3(b->threads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_batch_step<T, STATS>, (const BatchInst *)b->d_inst, b->n, b->tiles,
+                              (T *)b->pool, cur);
+}
+
 int launch(lbm_batch *b, cudaStream_t s, int cur, bool stats)
 {
-    const dim3 grid(b->grid), block(b->threads);
-    if (b->precision == LBM_FP16_SHIFTED) {
-        __half *pool = (__half *)b->pool;
-        if (stats)
-            k_batch_step<__half, true><<<grid, block, 0, s>>>(b->d_inst, b->n, b->tiles, pool, cur);
-        else
-            k_batch_step<__half, false><<<grid, block, 0, s>>>(b->d_inst, b->n, b->tiles, pool, cur);
-    } else {
-        float *pool = (float *)b->pool;
-        if (stats)
-            k_batch_step<float, true><<<grid, block, 0, s>>>(b->d_inst, b->n, b->tiles, pool, cur);
-        else
-            k_batch_step<float, false><<<grid, block, 0, s>>>(b->d_inst, b->n, b->tiles, pool, cur);
-    }
-    BK(cudaGetLastError());
+    cudaError_t e;
+    if (b->precision == LBM_FP16_SHIFTED)
+        e = stats ? launch_pdl<__half, true>(b, s, cur) : launch_pdl<__half, false>(b, s, cur);
+    else
+        e = stats ? launch_pdl<float, true>(b, s, cur) : launch_pdl<float, false>(b, s, cur);
+    if (e != cudaSuccess) return fail_cuda(e, "batch step launch");
     if (stats) {
         for (int i = 0; i < b->n; ++i) {
             lbm_handle *m = b->members[i];

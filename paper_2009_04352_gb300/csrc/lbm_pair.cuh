@@ -278,10 +278,25 @@ __device__ __forceinline__ void pair_tile(const T *__restrict__ src, T *__restri
     }
 }
 
+// Programmatic dependent launch: let the next step's grid start launching once
+// every CTA of this one is running, and wait for the previous grid (whose
+// output this step reads and whose input it overwrites) to complete before
+// touching global memory. Both are no-ops for ordinary launches.
+__device__ __forceinline__ void pdl_begin()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+#ifndef LBM_PAIR_MIN_BLOCKS
+#define LBM_PAIR_MIN_BLOCKS 6   // resident CTAs per SM the register budget must allow (80 registers)
+#endif
+
 template <typename T, bool STATS>
-__global__ void __launch_bounds__(128) k_step_pair(const T *__restrict__ src, T *__restrict__ dst, Geom g, Phys p,
+__global__ void __launch_bounds__(128, LBM_PAIR_MIN_BLOCKS) k_step_pair(const T *__restrict__ src, T *__restrict__ dst, Geom g, Phys p,
                                                    float *__restrict__ tw_out, double *__restrict__ part)
 {
+    pdl_begin();
     const int y = blockIdx.y, z = blockIdx.z;
     const long long blk = ((long long)y * g.nz + z) * gridDim.x + blockIdx.x;
     pair_tile<T, STATS>(src, dst, g, p, tw_out, STATS ? part + blk * K_PART : nullptr, blockIdx.x, y, z);
