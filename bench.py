@@ -33,9 +33,10 @@ BYTES_PER_LUP = {0: 152, 1: 76}     # 19 reads + 19 writes, FP32 / FP16 storage
 FALLBACK_HBM_GBS = 6800.0
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# dominant kernel from one ncu capture, keyed by workload; None until measured
-# for the current kernel build.
-NCU_TRAFFIC = {}
+# dominant kernel from one ncu capture of the current kernel build, keyed by
+# (workload, storage); profiles/k_step_pair_c2_256x64x128_fp32_launches.md has
+# the capture. Absent keys report null.
+NCU_TRAFFIC = {("c2", "fp32"): 267.6e6}
 
 
 def parse():
@@ -233,7 +234,10 @@ def workload_initial_populations(case):
 
 
 def cpu_baseline(case, budget_s=12.0):
-    """The FP64 oracle as it stands, single-threaded, on a bounded sample."""
+    """The FP64 oracle as it stands, single-threaded, on a bounded sample of the
+    workload. Returns the baseline record and the oracle's velocity field after
+    the sampled steps, with their count, so that the GPU error can be stated on
+    the same workload."""
     import oracle
     L = oracle.Lattice.from_case(case)
     L.init_channel(workload.u_mean_profile(case), workload.noise_amplitude(case), case.seed)
@@ -244,10 +248,30 @@ def cpu_baseline(case, budget_s=12.0):
     t0 = time.perf_counter()
     L.step(n)
     dt = time.perf_counter() - t0
+    _, u = L.moments()
     L.close()
-    return {"value": case.cells * n / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": f"FP64 oracle, {case.nx}x{case.ny}x{case.nz} WFB channel, {n} steps "
-                      f"after 1 warm-up step ({dt:.1f} s)"}
+    rec = {"value": case.cells * n / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+           "sample": f"FP64 oracle, {case.nx}x{case.ny}x{case.nz} WFB channel, {n} steps "
+                     f"after 1 warm-up step ({dt:.1f} s)"}
+    return rec, u, n + 1
+
+
+def stated_error(case, u_ref, steps, stream):
+    """Relative L_inf of the GPU velocity against the FP64 oracle after the same
+    steps from the same seeded field, FP32 and FP16 storage."""
+    import torch
+    from paper_2009_04352_gb300 import lbm
+    out = {}
+    for name, prec in (("fp32", lbm.FP32), ("fp16", lbm.FP16_SHIFTED)):
+        with torch.cuda.stream(stream):
+            ch = lbm.Channel.from_case(case, precision=prec, stream=stream.cuda_stream)
+            ch.init_channel(workload.u_mean_profile(case), workload.noise_amplitude(case), case.seed)
+            ch.step(steps)
+            _, u = ch.moments()
+            ch.close()
+        out[name] = float(np.max(np.abs(u - u_ref)) / np.max(np.abs(u_ref)))
+    return {"rel_linf_u": out, "steps": steps, "bound": {"fp32": 1e-5, "fp16": 5e-3},
+            "vs": "FP64 oracle, same seeded field, same workload"}
 
 
 def cpu_model():
@@ -381,8 +405,10 @@ def main():
     if variants:
         line["variants"] = variants
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(case)
-        line["cpu_baseline"]["cpu"] = cpu_model()
+        rec, u_ref, n_ref = cpu_baseline(case)
+        rec["cpu"] = cpu_model()
+        line["cpu_baseline"] = rec
+        line["err_vs_fp64"] = stated_error(case, u_ref, n_ref, stream)
     print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()

@@ -38,8 +38,12 @@ struct BatchInst {
     int nxb;            // tiles per row
 };
 
+#ifndef LBM_BATCH_MIN_BLOCKS
+#define LBM_BATCH_MIN_BLOCKS 5   // resident CTAs per SM the register budget must allow
+#endif
+
 template <typename T, bool STATS>
-__global__ void __launch_bounds__(128, 5) k_batch_step(const BatchInst *__restrict__ inst, int n, long long total,
+__global__ void __launch_bounds__(128, LBM_BATCH_MIN_BLOCKS) k_batch_step(const BatchInst *__restrict__ inst, int n, long long total,
                                                     T *__restrict__ pool, int cur)
 {
     lbm::pdl_begin();
