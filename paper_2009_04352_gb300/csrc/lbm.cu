@@ -333,6 +333,13 @@ int lbm_create_handle(lbm_grid g, double tau, double C_s, const double force[3],
     h->p.ekb = (float)exp(-wm.kappa * wm.B);
     h->p.y1_over_nu = (float)(wm.y1 / nu);
     h->p.newton_iters = wm.newton_iters > 0 ? wm.newton_iters : 12;
+    for (int c = 0; c < 3; ++c) h->p.hF[c] = (float)(0.5 * force[c]);
+    for (int k = 0; k < 9; ++k) {
+        const int a = 2 * k + 1;
+        const double eF = lbm::ex_of(a) * force[0] + lbm::ey_of(a) * force[1] + lbm::ez_of(a) * force[2];
+        h->p.weF[k] = (float)(lbm::w_of(a) * eF);
+    }
+    h->p.t02 = (float)((double)h->p.tau0 * (double)h->p.tau0);
     h->precision = precision;
     h->layout = layout;
     h->stream = (cudaStream_t)cuda_stream;

@@ -70,6 +70,10 @@ struct Phys {
     float ekb;           // exp(-kappa B)
     float y1_over_nu;    // y1 / nu of the wall law
     int newton_iters;
+    // derived on the host once, so kernels do not recompute them per tile
+    float hF[3];         // F / 2
+    float weF[9];        // w_k (e_k . F) for the opposite pairs k = 0..8 (directions 2k+1, 2k+2)
+    float t02;           // tau0^2
 };
 
 template <typename T> __device__ __forceinline__ float ld(const T *p);

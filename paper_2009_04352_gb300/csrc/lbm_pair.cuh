@@ -99,32 +99,45 @@ struct PairState {
 // and the update of the pair is  delta_a = de + dd,  delta_b = de - dd  with
 //   de = omega w (S0 + 9/2 rho (e.u)^2) - 3 w gk u.F + 9 w gk (e.u)(e.F) - omega s / 2
 //   dd = 3 omega w rho (e.u) + 3 w gk (e.F) - omega d / 2.
-// Only s and d are kept through the collision (the new populations are
-// (s' + d') / 2 and (s' - d') / 2), which keeps 18 fewer values live.
+// Only the half sums and differences s/2, d/2 are kept through the collision
+// (the new populations are their sum and difference), which keeps 18 fewer
+// values live.
 __device__ __forceinline__ PairState collide_pair(float2 (&f)[Q], const Phys &p)
 {
     PairState c;
-    float2 sk[9], dk[9];
+    // half sums and half differences of the pairs: f_a = hs + hd, f_b = hs - hd
+    float2 hs[9], hd[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-        sk[k] = add2(f[2 * k + 1], f[2 * k + 2]);
-        dk[k] = sub2(f[2 * k + 1], f[2 * k + 2]);
+        hs[k] = mul2(bc(0.5f), add2(f[2 * k + 1], f[2 * k + 2]));
+        hd[k] = mul2(bc(0.5f), sub2(f[2 * k + 1], f[2 * k + 2]));
     }
-    const float2 drho = add2(add2(add2(f[0], sk[0]), add2(sk[1], sk[2])),
-                             add2(add2(add2(sk[3], sk[4]), add2(sk[5], sk[6])), add2(sk[7], sk[8])));
-    const float2 jx = add2(add2(dk[0], dk[3]), add2(add2(dk[4], dk[6]), dk[7]));
-    const float2 jy = add2(add2(dk[1], dk[3]), add2(sub2(dk[5], dk[6]), dk[8]));
-    const float2 jz = sub2(add2(add2(dk[2], dk[4]), dk[5]), add2(dk[7], dk[8]));
-    float2 pxx = add2(add2(sk[0], sk[3]), add2(add2(sk[4], sk[6]), sk[7]));
-    float2 pyy = add2(add2(sk[1], sk[3]), add2(add2(sk[5], sk[6]), sk[8]));
-    float2 pzz = add2(add2(sk[2], sk[4]), add2(add2(sk[5], sk[7]), sk[8]));
-    float2 pxy = sub2(sk[3], sk[6]);
-    float2 pxz = sub2(sk[4], sk[7]);
-    float2 pyz = sub2(sk[5], sk[8]);
+    // doubling by addition (exact) keeps constants out of the packed ops
+    const float2 shs = add2(add2(add2(hs[0], hs[1]), add2(hs[2], hs[3])),
+                            add2(add2(hs[4], hs[5]), add2(add2(hs[6], hs[7]), hs[8])));
+    const float2 drho = add2(add2(shs, shs), f[0]);
+    float2 jx = add2(add2(hd[0], hd[3]), add2(add2(hd[4], hd[6]), hd[7]));
+    float2 jy = add2(add2(hd[1], hd[3]), add2(sub2(hd[5], hd[6]), hd[8]));
+    float2 jz = sub2(add2(add2(hd[2], hd[4]), hd[5]), add2(hd[7], hd[8]));
+    jx = add2(jx, jx);
+    jy = add2(jy, jy);
+    jz = add2(jz, jz);
+    float2 pxx = add2(add2(hs[0], hs[3]), add2(add2(hs[4], hs[6]), hs[7]));
+    float2 pyy = add2(add2(hs[1], hs[3]), add2(add2(hs[5], hs[6]), hs[8]));
+    float2 pzz = add2(add2(hs[2], hs[4]), add2(add2(hs[5], hs[7]), hs[8]));
+    float2 pxy = sub2(hs[3], hs[6]);
+    float2 pxz = sub2(hs[4], hs[7]);
+    float2 pyz = sub2(hs[5], hs[8]);
+    pxx = add2(pxx, pxx);
+    pyy = add2(pyy, pyy);
+    pzz = add2(pzz, pzz);
+    pxy = add2(pxy, pxy);
+    pxz = add2(pxz, pxz);
+    pyz = add2(pyz, pyz);
 
     c.rho = add2(bc(1.f), drho);
     const float2 idev = make_float2(-drho.x / c.rho.x, -drho.y / c.rho.y);   // 1/rho - 1
-    const float2 jfx = add2(jx, bc(0.5f * p.Fx)), jfy = add2(jy, bc(0.5f * p.Fy)), jfz = add2(jz, bc(0.5f * p.Fz));
+    const float2 jfx = add2(jx, bc(p.hF[0])), jfy = add2(jy, bc(p.hF[1])), jfz = add2(jz, bc(p.hF[2]));
     c.ux = fma2(jfx, idev, jfx);
     c.uy = fma2(jfy, idev, jfy);
     c.uz = fma2(jfz, idev, jfz);
@@ -138,18 +151,18 @@ __device__ __forceinline__ PairState collide_pair(float2 (&f)[Q], const Phys &p)
     pxy = sub2(pxy, mul2(rux, uy));
     pxz = sub2(pxz, mul2(rux, uz));
     pyz = sub2(pyz, mul2(ruy, uz));
-    const float2 q2 = fma2(bc(2.f), fma2(pxy, pxy, fma2(pxz, pxz, mul2(pyz, pyz))),
-                           fma2(pxx, pxx, fma2(pyy, pyy, mul2(pzz, pzz))));
+    const float2 qo = fma2(pxy, pxy, fma2(pxz, pxz, mul2(pyz, pyz)));
+    const float2 q2 = add2(add2(qo, qo), fma2(pxx, pxx, fma2(pyy, pyy, mul2(pzz, pzz))));
+    // omega = 1 / tau_eff = 2 / (tau0 + sqrt(tau0^2 + smag |Pi_neq| / rho)),
+    // 1/rho = 1 + idev (a sum of positive terms: no cancellation)
     float2 omega;
     {
-        const float t02 = p.tau0 * p.tau0;
-        const float cqx = p.smag * sqrtf(q2.x) / rho.x, cqy = p.smag * sqrtf(q2.y) / rho.y;
-        const float tx = p.tau0 + cqx / (2.f * (sqrtf(t02 + cqx) + p.tau0));
-        const float ty = p.tau0 + cqy / (2.f * (sqrtf(t02 + cqy) + p.tau0));
-        omega = make_float2(1.f / tx, 1.f / ty);
+        const float t02 = p.t02;
+        const float cqx = p.smag * sqrtf(q2.x) * (1.f + idev.x), cqy = p.smag * sqrtf(q2.y) * (1.f + idev.y);
+        omega = make_float2(2.f / (p.tau0 + sqrtf(t02 + cqx)), 2.f / (p.tau0 + sqrtf(t02 + cqy)));
     }
     const float2 gk = fma2(bc(-0.5f), omega, bc(1.f));
-    const float2 hw = mul2(bc(-0.5f), omega);                              // -omega / 2
+    const float2 nw = mul2(bc(-1.f), omega);                               // -omega
     const float2 usq = fma2(ux, ux, fma2(uy, uy, mul2(uz, uz)));
     const float2 uF = fma2(ux, bc(p.Fx), fma2(uy, bc(p.Fy), mul2(uz, bc(p.Fz))));
     const float2 S0 = fma2(bc(-1.5f), mul2(rho, usq), drho);
@@ -162,38 +175,42 @@ __device__ __forceinline__ PairState collide_pair(float2 (&f)[Q], const Phys &p)
     const float2 Aa = mul2(bc(1.f / 18.f), oR45), Ad = mul2(bc(1.f / 36.f), oR45);
     const float2 Da = mul2(bc(1.f / 18.f), oR3), Dd = mul2(bc(1.f / 36.f), oR3);
 
-    float2 mass = bc(0.f), mx = bc(0.f), my = bc(0.f), mz = bc(0.f);
+    // e.u of the odd member of each pair (directions 1, 3, 5, 7, 9, 11, 13, 15, 17)
+    const float2 eus[9] = {ux, uy, uz, add2(ux, uy), add2(ux, uz), add2(uy, uz),
+                           sub2(ux, uy), sub2(ux, uz), sub2(uy, uz)};
+    float2 mass, mx, my, mz;
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
         const int a = 2 * k + 1;
         const bool axis = k < 3;
-        const float wk = axis ? 1.f / 18.f : 1.f / 36.f;
-        float2 eu = bc(0.f);
-        if (ex_of(a)) eu = ex_of(a) > 0 ? add2(eu, ux) : sub2(eu, ux);
-        if (ey_of(a)) eu = ey_of(a) > 0 ? add2(eu, uy) : sub2(eu, uy);
-        if (ez_of(a)) eu = ez_of(a) > 0 ? add2(eu, uz) : sub2(eu, uz);
-        const float eFs = wk * (ex_of(a) * p.Fx + ey_of(a) * p.Fy + ez_of(a) * p.Fz);   // w e.F
-        const float2 Gk = mul2(g9, bc(eFs)), Hk = mul2(g3, bc(eFs));
-        const float2 de = fma2(hw, sk[k], fma2(fma2(axis ? Aa : Ad, eu, Gk), eu, axis ? Ca : Cd));
-        const float2 dd = fma2(hw, dk[k], fma2(axis ? Da : Dd, eu, Hk));
-        mass = add2(mass, de);
-        if (ex_of(a)) mx = ex_of(a) > 0 ? add2(mx, dd) : sub2(mx, dd);
-        if (ey_of(a)) my = ey_of(a) > 0 ? add2(my, dd) : sub2(my, dd);
-        if (ez_of(a)) mz = ez_of(a) > 0 ? add2(mz, dd) : sub2(mz, dd);
-        // the pair's new sum and difference (delta_a = de + dd, delta_b = de - dd)
-        sk[k] = fma2(bc(2.f), de, sk[k]);
-        dk[k] = fma2(bc(2.f), dd, dk[k]);
+        const float2 eu = eus[k];
+        const float2 eF = bc(p.weF[k]);   // w e.F
+        const float2 Gk = mul2(g9, eF), Hk = mul2(g3, eF);
+        // with s = 2 hs and d = 2 hd: -omega s / 2 = -omega hs
+        const float2 de = fma2(nw, hs[k], fma2(fma2(axis ? Aa : Ad, eu, Gk), eu, axis ? Ca : Cd));
+        const float2 dd = fma2(nw, hd[k], fma2(axis ? Da : Dd, eu, Hk));
+        // accumulate sum de and sum e dd (first terms: pairs 0, 1, 2 are the axes)
+        mass = k == 0 ? de : add2(mass, de);
+        if (k == 0) mx = dd;
+        else if (ex_of(a)) mx = ex_of(a) > 0 ? add2(mx, dd) : sub2(mx, dd);
+        if (k == 1) my = dd;
+        else if (k > 1 && ey_of(a)) my = ey_of(a) > 0 ? add2(my, dd) : sub2(my, dd);
+        if (k == 2) mz = dd;
+        else if (k > 2 && ez_of(a)) mz = ez_of(a) > 0 ? add2(mz, dd) : sub2(mz, dd);
+        // the pair's new half sum and half difference (delta_a = de + dd, delta_b = de - dd)
+        hs[k] = add2(hs[k], de);
+        hd[k] = add2(hd[k], dd);
     }
     // exact momentum F and mass 0 of the update (see collide()): the axis pairs
     // take the momentum residual, the rest population the mass residual
-    dk[0] = fma2(bc(2.f), sub2(bc(0.5f * p.Fx), mx), dk[0]);
-    dk[1] = fma2(bc(2.f), sub2(bc(0.5f * p.Fy), my), dk[1]);
-    dk[2] = fma2(bc(2.f), sub2(bc(0.5f * p.Fz), mz), dk[2]);
-    f[0] = fma2(bc(-2.f), mass, f[0]);
+    hd[0] = add2(hd[0], sub2(bc(p.hF[0]), mx));
+    hd[1] = add2(hd[1], sub2(bc(p.hF[1]), my));
+    hd[2] = add2(hd[2], sub2(bc(p.hF[2]), mz));
+    f[0] = sub2(f[0], add2(mass, mass));
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-        f[2 * k + 1] = mul2(bc(0.5f), add2(sk[k], dk[k]));
-        f[2 * k + 2] = mul2(bc(0.5f), sub2(sk[k], dk[k]));
+        f[2 * k + 1] = add2(hs[k], hd[k]);
+        f[2 * k + 2] = sub2(hs[k], hd[k]);
     }
     return c;
 }
