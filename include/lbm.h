@@ -91,12 +91,15 @@ typedef enum {
  *   TMA:  two cells per thread; each CTA streams whole source rows into a
  *         shared-memory ring with bulk asynchronous copies (full/empty
  *         mbarriers, 2-4 stages); nx a multiple of 64 whose rows fit the ring.
- *   AUTO: PAIR for even nx, else CELL. */
+ *   QUAD: four cells per thread, 8-byte loads and stores; FP16 storage and nx a
+ *         multiple of 4.
+ *   AUTO: QUAD where allowed, else PAIR for even nx, else CELL. */
 typedef enum {
     LBM_KERNEL_AUTO = 0,
     LBM_KERNEL_CELL = 1,
     LBM_KERNEL_PAIR = 2,
-    LBM_KERNEL_TMA = 3
+    LBM_KERNEL_TMA = 3,
+    LBM_KERNEL_QUAD = 4
 } lbm_kernel;
 
 typedef struct lbm_handle lbm_handle;

@@ -10,7 +10,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblbm.so")
 SOURCES = ["lbm.cu", "lbm_noalloc.cu", "lbm_batch.cu"]
-HEADERS = ["lbm_device.cuh", "lbm_kernels.cuh", "lbm_pair.cuh", "lbm_tma.cuh", "lbm_handle.h"]
+HEADERS = ["lbm_device.cuh", "lbm_kernels.cuh", "lbm_pair.cuh", "lbm_tma.cuh", "lbm_handle.h", "lbm_quad.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -8,6 +8,7 @@
 #include <algorithm>
 
 #include "lbm.h"
+#include "lbm_quad.cuh"
 #include "lbm_tma.cuh"
 
 namespace {
@@ -46,9 +47,11 @@ size_t elem_size(const lbm_handle *h) { return h->precision == LBM_FP16_SHIFTED 
 dim3 grid_of(const lbm_handle *h, int bx) { return dim3((h->g.nx + bx - 1) / bx, h->g.ny, h->g.nz); }
 
 // grid of the step kernel: one thread per cell, or per x-pair for even nx
+int cells_per_thread(int kernel) { return kernel == LBM_KERNEL_CELL ? 1 : (kernel == LBM_KERNEL_QUAD ? 4 : 2); }
+
 dim3 step_grid(const lbm_handle *h)
 {
-    const int per_row = h->kernel == LBM_KERNEL_CELL ? h->g.nx : h->g.nx / 2;
+    const int per_row = h->g.nx / cells_per_thread(h->kernel);
     return dim3((per_row + h->bx - 1) / h->bx, h->g.ny, h->g.nz);
 }
 
@@ -58,14 +61,18 @@ int select_kernel(lbm_handle *h, int kernel)
 {
     const bool even = (h->g.nx % 2) == 0;
     const bool seg = (h->g.nx % 64) == 0;
-    // AUTO: the two-cell kernel where nx is even (measured fastest on GB300 for
-    // every benchmark grid in both storage precisions), else the one-cell kernel
-    if (kernel == LBM_KERNEL_AUTO) kernel = even ? LBM_KERNEL_PAIR : LBM_KERNEL_CELL;
+    const bool quad = (h->g.nx % 4) == 0 && h->precision == LBM_FP16_SHIFTED;
+    // AUTO: FP16 storage with nx a multiple of 4 runs the four-cell kernel, else
+    // the two-cell kernel where nx is even, else the one-cell kernel (measured
+    // fastest in that order on GB300 for every benchmark grid)
+    if (kernel == LBM_KERNEL_AUTO) kernel = quad ? LBM_KERNEL_QUAD : (even ? LBM_KERNEL_PAIR : LBM_KERNEL_CELL);
     if (kernel == LBM_KERNEL_PAIR && !even) return fail(LBM_ERR_ARG, "two-cell kernel needs an even nx");
+    if (kernel == LBM_KERNEL_QUAD && !quad)
+        return fail(LBM_ERR_ARG, "four-cell kernel needs FP16 storage and nx a multiple of 4");
     if (kernel == LBM_KERNEL_TMA && !seg) return fail(LBM_ERR_ARG, "pipelined kernel needs nx a multiple of 64");
-    if (kernel < LBM_KERNEL_CELL || kernel > LBM_KERNEL_TMA) return fail(LBM_ERR_ARG, "unknown kernel");
+    if (kernel < LBM_KERNEL_CELL || kernel > LBM_KERNEL_QUAD) return fail(LBM_ERR_ARG, "unknown kernel");
     h->kernel = kernel;
-    const int per_row = kernel == LBM_KERNEL_CELL ? h->g.nx : h->g.nx / 2;
+    const int per_row = h->g.nx / cells_per_thread(kernel);
     h->bx = per_row >= 128 ? 128 : (per_row > 32 ? 64 : 32);   // <= the kernels' launch bound of 128
     if (kernel == LBM_KERNEL_TMA) {
         const int rc = configure_rows(h);
@@ -198,6 +205,23 @@ cudaError_t launch_pair_pdl(lbm_handle *h, cudaStream_t s, dim3 grid, dim3 block
     return cudaLaunchKernelEx(&cfg, lbm::k_step_pair<T, STATS>, (const T *)a, (T *)b, h->g, h->p, h->tw, h->part);
 }
 
+template <bool STATS>
+cudaError_t launch_quad_pdl(lbm_handle *h, cudaStream_t s, dim3 grid, dim3 block, const void *a, void *b)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, lbm::k_step_quad<STATS>, (const __half *)a, (__half *)b, h->g, h->p, h->tw,
+                              h->part);
+}
+
 int launch_step(lbm_handle *h, cudaStream_t s, int src, bool stats)
 {
     const dim3 grid = step_grid(h), block(h->bx);
@@ -205,6 +229,10 @@ int launch_step(lbm_handle *h, cudaStream_t s, int src, bool stats)
     void *b = h->f[src ^ 1];
     if (h->kernel == LBM_KERNEL_TMA) {
         launch_tma(h, s, src, stats);
+    } else if (h->kernel == LBM_KERNEL_QUAD) {
+        const cudaError_t e = stats ? launch_quad_pdl<true>(h, s, grid, block, a, b)
+                                    : launch_quad_pdl<false>(h, s, grid, block, a, b);
+        if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "step launch: %s", cudaGetErrorString(e));
     } else if (h->kernel == LBM_KERNEL_PAIR) {
         cudaError_t e;
         if (h->precision == LBM_FP16_SHIFTED)

@@ -1,0 +1,204 @@
+// Four cells per thread for FP16 storage (nx a multiple of 4).
+//
+// FP16 storage halves the bytes per cell, so the per-cell instruction count,
+// not DRAM, bounds the two-cell kernel. Here a thread owns the x-quad
+// (x0 .. x0 + 3): every population is one aligned 8-byte load of four halves,
+// an x-shifted direction costs one warp shuffle and two byte permutes for four
+// cells, and every store is one 8-byte store, so the address, load, shuffle
+// and store instructions per cell are half those of the two-cell form. The
+// collision runs as two packed pairs (collide_pair of lbm_pair.cuh), one after
+// the other, on the same raw registers.
+#pragma once
+
+#include "lbm_pair.cuh"
+
+namespace lbm {
+
+__device__ __forceinline__ float2 h2f(uint32_t w)
+{
+    __half2 h = *reinterpret_cast<__half2 *>(&w);
+    return __half22float2(h);
+}
+
+__device__ __forceinline__ uint32_t f2h(float2 v)
+{
+    __half2 h = __floats2half2_rn(v.x, v.y);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+
+// Four halves of one source row for cells x0 .. x0 + 3 shifted by SH (cell x
+// reads x - SH), as two 32-bit words (x0, x0 + 1 | x0 + 2, x0 + 3), lower
+// element in the low half.
+template <int SH>
+__device__ __forceinline__ uint2 row_quad(const __half *__restrict__ row, int x0, int nx, int lane)
+{
+    const uint2 v = __ldg(reinterpret_cast<const uint2 *>(row + x0));
+    if (SH == 0) return v;
+    if (SH == 1) {   // (x0 - 1, x0 | x0 + 1, x0 + 2)
+        uint32_t lw = __shfl_up_sync(0xffffffffu, v.y, 1);   // (x0 - 2, x0 - 1) of the left lane
+        if (lane == 0 || x0 == 0) {
+            const int xl = x0 == 0 ? nx - 1 : x0 - 1;
+            lw = (uint32_t)__ldg(reinterpret_cast<const unsigned short *>(row + xl)) << 16;
+        }
+        return make_uint2(__byte_perm(lw, v.x, 0x5432), __byte_perm(v.x, v.y, 0x5432));
+    }
+    // SH == -1: (x0 + 1, x0 + 2 | x0 + 3, x0 + 4)
+    uint32_t rw = __shfl_down_sync(0xffffffffu, v.x, 1);     // (x0 + 4, x0 + 5) of the right lane
+    if (lane == 31 || x0 + 4 >= nx) {
+        const int xr = x0 + 4 >= nx ? x0 + 4 - nx : x0 + 4;
+        rw = (uint32_t)__ldg(reinterpret_cast<const unsigned short *>(row + xr));
+    }
+    return make_uint2(__byte_perm(v.x, v.y, 0x5432), __byte_perm(v.y, rw, 0x5432));
+}
+
+// Gather of the quad (streaming with the wall reflection of src_offset).
+template <int ROW>
+__device__ __forceinline__ void gather_quad(const __half *__restrict__ src, const Geom &g, int wall, int x0, int y,
+                                            int z, int zm, int zp, int lane, uint2 (&r)[Q])
+{
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        const int ex = ex_of(a), ey = ey_of(a), ez = ez_of(a);
+        const bool crosses = (ROW == ROW_BOTTOM && ey == 1) || (ROW == ROW_TOP && ey == -1);
+        const int zs = ez == 1 ? zm : (ez == -1 ? zp : z);
+        if (!crosses) {
+            const __half *row = src + (long long)a * g.plane + ((long long)zs * g.ny + (y - ey)) * g.sx;
+            if (ex == 1)
+                r[a] = row_quad<1>(row, x0, g.nx, lane);
+            else if (ex == -1)
+                r[a] = row_quad<-1>(row, x0, g.nx, lane);
+            else
+                r[a] = row_quad<0>(row, x0, g.nx, lane);
+        } else if (wall == WALL_BB) {
+            const __half *row = src + (long long)opp_of(a) * g.plane + ((long long)z * g.ny + y) * g.sx;
+            r[a] = row_quad<0>(row, x0, g.nx, lane);
+        } else {
+            const __half *row = src + (long long)mirror_of(a) * g.plane + ((long long)zs * g.ny + y) * g.sx;
+            if (ex == 1)
+                r[a] = row_quad<1>(row, x0, g.nx, lane);
+            else if (ex == -1)
+                r[a] = row_quad<-1>(row, x0, g.nx, lane);
+            else
+                r[a] = row_quad<0>(row, x0, g.nx, lane);
+        }
+    }
+}
+
+// Collision (and wall layer) of one packed pair held in word H of the quad.
+template <int H, bool STATS>
+__device__ __forceinline__ void quad_half(uint2 (&r)[Q], const Phys &p, bool wall_row, bool bottom, float4 &tw,
+                                          double (&v)[K_PART], bool valid)
+{
+    float2 f[Q];
+#pragma unroll
+    for (int a = 0; a < Q; ++a) f[a] = h2f(H ? r[a].y : r[a].x);
+    const PairState c = collide_pair(f, p);
+    float2 twx = bc(0.f), twz = bc(0.f);
+    if (wall_row) {
+        float fa[Q], fb[Q];
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            fa[a] = f[a].x;
+            fb[a] = f[a].y;
+        }
+        const CellState ca{c.rho.x, c.ux.x, c.uy.x, c.uz.x}, cb{c.rho.y, c.ux.y, c.uy.y, c.uz.y};
+        wall_layer(fa, ca, p, bottom, 0xffffffffu, twx.x, twz.x);
+        wall_layer(fb, cb, p, bottom, 0xffffffffu, twx.y, twz.y);
+#pragma unroll
+        for (int a = 0; a < Q; ++a) f[a] = make_float2(fa[a], fb[a]);
+        tw = make_float4(twx.x, twz.x, twx.y, twz.y);
+    }
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        if (H)
+            r[a].y = f2h(f[a]);
+        else
+            r[a].x = f2h(f[a]);
+    }
+    if (STATS && valid) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const double rr = h ? c.rho.y : c.rho.x, ux = h ? c.ux.y : c.ux.x, uy = h ? c.uy.y : c.uy.x,
+                         uz = h ? c.uz.y : c.uz.x;
+            const double tx = h ? twx.y : twx.x, tz = h ? twz.y : twz.x, m2 = tx * tx + tz * tz;
+            v[0] += rr;
+            v[1] += ux;
+            v[2] += uy;
+            v[3] += uz;
+            v[4] += ux * ux;
+            v[5] += uy * uy;
+            v[6] += uz * uz;
+            v[7] += ux * uy;
+            v[8] += rr * ux;
+            v[9] += rr * uy;
+            v[10] += rr * uz;
+            v[11] += tx;
+            v[12] += tz;
+            v[13] += sqrt(m2);
+            v[14] += m2;
+        }
+    }
+}
+
+#ifndef LBM_QUAD_MIN_BLOCKS
+#define LBM_QUAD_MIN_BLOCKS 5   // resident CTAs per SM the register budget must allow
+#endif
+
+// One tile: the x-quads xb * blockDim.x + threadIdx.x of row (y, z), i.e.
+// cells [4 xb blockDim.x, 4 (xb + 1) blockDim.x). With STATS the block writes
+// its FP64 partial sums to part_blk[0..K_PART).
+template <bool STATS>
+__device__ __forceinline__ void quad_tile(const __half *__restrict__ src, __half *__restrict__ dst, const Geom &g,
+                                          const Phys &p, float *__restrict__ tw_out, double *__restrict__ part_blk,
+                                          int xb, int y, int z)
+{
+    const int lane = threadIdx.x & 31;
+    const int x0 = 4 * (xb * blockDim.x + threadIdx.x);
+    const bool valid = x0 < g.nx;
+    const int xl = valid ? x0 : g.nx - 4;   // lanes past the row end read in bounds and store nothing
+    const int zm = z == 0 ? g.nz - 1 : z - 1, zp = z == g.nz - 1 ? 0 : z + 1;
+
+    uint2 r[Q];
+    if (y == 0)
+        gather_quad<ROW_BOTTOM>(src, g, p.wall, xl, y, z, zm, zp, lane, r);
+    else if (y == g.ny - 1)
+        gather_quad<ROW_TOP>(src, g, p.wall, xl, y, z, zm, zp, lane, r);
+    else
+        gather_quad<ROW_INTERIOR>(src, g, p.wall, xl, y, z, zm, zp, lane, r);
+
+    const bool wall_row = y == 0 || y == g.ny - 1;
+    double v[K_PART];
+    if (STATS) {
+#pragma unroll
+        for (int k = 0; k < K_PART; ++k) v[k] = 0.0;
+    }
+    float4 twa = make_float4(0.f, 0.f, 0.f, 0.f), twb = twa;
+    quad_half<0, STATS>(r, p, wall_row, y == 0, twa, v, valid);
+    quad_half<1, STATS>(r, p, wall_row, y == 0, twb, v, valid);
+    if (valid) {
+        if (wall_row) {
+            float4 *t = reinterpret_cast<float4 *>(reinterpret_cast<float2 *>(tw_out) +
+                                                   ((long long)((y == 0 ? 0 : 1) * g.nz + z) * g.nx + x0));
+            t[0] = twa;
+            t[1] = twb;
+        }
+        __half *d = dst + ((long long)z * g.ny + y) * g.sx + x0;
+#pragma unroll
+        for (int a = 0; a < Q; ++a) *reinterpret_cast<uint2 *>(d + a * g.plane) = r[a];
+    }
+    if (STATS) block_reduce_store<K_PART>(v, part_blk);
+}
+
+template <bool STATS>
+__global__ void __launch_bounds__(128, LBM_QUAD_MIN_BLOCKS) k_step_quad(const __half *__restrict__ src,
+                                                                         __half *__restrict__ dst, Geom g, Phys p,
+                                                                         float *__restrict__ tw_out,
+                                                                         double *__restrict__ part)
+{
+    pdl_begin();
+    const int y = blockIdx.y, z = blockIdx.z;
+    const long long blk = ((long long)y * g.nz + z) * gridDim.x + blockIdx.x;
+    quad_tile<STATS>(src, dst, g, p, tw_out, STATS ? part + blk * K_PART : nullptr, blockIdx.x, y, z);
+}
+
+}  // namespace lbm

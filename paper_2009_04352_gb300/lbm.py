@@ -28,7 +28,7 @@ LBM_ERR_DIVERGED = -4
 LBM_ERR_STATE = -5
 
 WALL_BB, WALL_WFB, WALL_FREESLIP = 0, 1, 2
-KERNEL_AUTO, KERNEL_CELL, KERNEL_PAIR, KERNEL_TMA = 0, 1, 2, 3
+KERNEL_AUTO, KERNEL_CELL, KERNEL_PAIR, KERNEL_TMA, KERNEL_QUAD = 0, 1, 2, 3, 4
 FP32, FP16_SHIFTED = 0, 1
 PULL2 = 0
 

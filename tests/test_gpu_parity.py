@@ -74,7 +74,7 @@ RAGGED = [SMALL.with_(nx=37, ny=6, nz=5), SMALL.with_(nx=1, ny=8, nz=1),
           SMALL.with_(nx=34, ny=2, nz=3), SMALL.with_(nx=300, ny=3, nz=2),
           SMALL.with_(nx=64, ny=2, nz=3), SMALL.with_(nx=192, ny=5, nz=2),
           SMALL.with_(nx=128, ny=3, nz=1)]
-KERNELS = [lbm.KERNEL_TMA, lbm.KERNEL_PAIR, lbm.KERNEL_CELL]
+KERNELS = [lbm.KERNEL_TMA, lbm.KERNEL_PAIR, lbm.KERNEL_CELL, lbm.KERNEL_QUAD]
 
 
 @pytest.mark.parametrize("precision", [lbm.FP32, lbm.FP16_SHIFTED])
@@ -95,6 +95,8 @@ def test_init_matches_oracle(precision):
 @pytest.mark.parametrize("wall", WALLS)
 def test_parity_100_steps(wall, precision, kernel):
     """64x32x32 channel, tau0 0.52, C_s 0.1, seeded log-law + 10% noise: 100 steps."""
+    if kernel == lbm.KERNEL_QUAD and precision != lbm.FP16_SHIFTED:
+        pytest.skip("the four-cell kernel serves FP16 storage only")
     case = SMALL
     checkpoints = (1, 10, 50, 100)
     ref = oracle_run(case, wall, checkpoints)
@@ -282,4 +284,30 @@ def test_kernel_selection_rules():
     assert ch.kernel == lbm.KERNEL_PAIR
     ch.set_kernel(lbm.KERNEL_TMA)
     assert ch.kernel == lbm.KERNEL_TMA
+    with pytest.raises(lbm.LbmError):
+        ch.set_kernel(lbm.KERNEL_QUAD)          # FP32 storage
     ch.close()
+    ch = lbm.Channel.from_case(case.with_(nx=128), precision=lbm.FP16_SHIFTED)
+    assert ch.kernel == lbm.KERNEL_QUAD
+    ch.close()
+
+
+def test_quad_and_pair_kernels_agree_bitwise():
+    """FP16 four-cell and two-cell kernels run the same per-cell arithmetic."""
+    case = SMALL.with_(nx=300, ny=8, nz=6)
+    a = gpu_channel(case, workload.WALL_WFB, lbm.FP16_SHIFTED, lbm.KERNEL_QUAD)
+    b = gpu_channel(case, workload.WALL_WFB, lbm.FP16_SHIFTED, lbm.KERNEL_PAIR)
+    for ch in (a, b):
+        ch.set_stats_every(4)
+        ch.step(37)
+    assert np.array_equal(a.populations(), b.populations())
+    assert np.array_equal(a.wall_stress(), b.wall_stress())
+    sa, wa, na = a.plane_stats()
+    sb, wb, nb = b.plane_stats()
+    assert na == nb == 10
+    assert np.allclose(sa, sb, rtol=1e-12, atol=1e-12 * np.max(np.abs(sb)))
+    # the FP32 wall stress of a sampled step may differ in its last bit between
+    # the two forms (FP16 storage of the populations hides it)
+    assert np.allclose(wa, wb, rtol=1e-7, atol=1e-7 * np.max(np.abs(wb)))
+    a.close()
+    b.close()
