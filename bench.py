@@ -36,7 +36,7 @@ FALLBACK_HBM_GBS = 6800.0
 # dominant kernel from one ncu capture of the current kernel build, keyed by
 # (workload, storage); profiles/k_step_pair_c2_256x64x128_fp32_launches.md has
 # the capture. Absent keys report null.
-NCU_TRAFFIC = {("c2", "fp32"): 267.6e6}
+NCU_TRAFFIC = {("c2", "fp32"): 264.5e6}
 
 
 def parse():
@@ -117,6 +117,20 @@ class ClockSampler:
         reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i].lower() == "active"})
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(self.rows)}
+
+
+def whole_job_rate(local_cells, steps, local_ms, dist=None, device="cpu"):
+    """Whole-job throughput of N replicas: the cells of all ranks times the
+    steps, over the slowest rank's time. Returns (MLUPS, max ms, total cells)."""
+    import torch
+    if dist is None or not dist.is_initialized():
+        return local_cells * steps / (local_ms * 1e-3) / 1e6, local_ms, local_cells
+    t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+    c = torch.tensor([float(local_cells)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    ms, cells = float(t.item()), int(c.item())
+    return cells * steps / (ms * 1e-3) / 1e6, ms, cells
 
 
 def dist_env():
@@ -341,14 +355,10 @@ def main():
     torch.cuda.synchronize()
     ms, finite = time_channel(case, precision, args.steps, args.warmup, stream, clocks)
     torch.cuda.synchronize()
-    if pg:
-        t = torch.tensor([ms], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
-        pg.barrier()
-    total_cells = case.cells * world
-    mlups = total_cells * args.steps / (ms * 1e-3) / 1e6
     per_gpu_mlups = case.cells * args.steps / (ms * 1e-3) / 1e6
+    mlups, ms, total_cells = whole_job_rate(case.cells, args.steps, ms, pg, "cuda")
+    if pg:
+        pg.barrier()
     kernel_ms = ms / args.steps
     achieved = BYTES_PER_LUP[precision] * case.cells / (kernel_ms * 1e-3) / 1e9
 
@@ -356,11 +366,8 @@ def main():
     if not args.no_e2e:
         e2e_steps = min(args.steps, 2000)
         e_ms, h2d, d2h = e2e_channel(case, precision, e2e_steps, stream)
-        if pg:
-            t = torch.tensor([e_ms], device="cuda")
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            e_ms = float(t.item())
-        e2e = {"value": total_cells * e2e_steps / (e_ms * 1e-3) / 1e6, "unit": "MLUPS",
+        e_val, e_ms, _ = whole_job_rate(case.cells, e2e_steps, e_ms, pg, "cuda")
+        e2e = {"value": e_val, "unit": "MLUPS",
                "h2d_bytes_per_step": h2d / e2e_steps, "d2h_bytes_per_step": d2h / e2e_steps,
                "steps": e2e_steps,
                "what": "C-ABI with host buffers: pinned FP64 initial field uploaded, steps with "
