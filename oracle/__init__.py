@@ -83,6 +83,12 @@ def _load():
             "or_plane_stats": (None, [vp, dp, dp, C.POINTER(C.c_longlong), C.c_int]),
             "or_get_step": (C.c_longlong, [vp]),
             "or_step": (None, [vp, C.c_int]),
+            "or_mrt_matrix": (None, [dp]),
+            "or_mrt_rates": (None, [C.c_double, dp]),
+            "or_collide_mrt": (None, [dp, C.c_double, C.c_double, dp, C.c_double, dp, dp, dp, dp]),
+            "or_collide_mrt_rates": (None, [dp, C.c_double, C.c_double, dp, C.c_double, dp, dp, dp, dp, dp]),
+            "or_van_driest": (C.c_double, [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double]),
+            "or_set_les": (None, [vp, C.c_int, C.c_double, C.c_double]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -156,6 +162,43 @@ def collide(f, tau0, cs, F):
     _load().or_collide(_dp(_vec(f, 19)), float(tau0), float(cs), _dp(_vec(F, 3)), _dp(fs),
                        _dp(rho), _dp(u), _dp(tau))
     return fs, rho[0], u, tau[0]
+
+
+def mrt_matrix():
+    out = np.zeros(19 * 19)
+    _load().or_mrt_matrix(_dp(out))
+    return out.reshape(19, 19)
+
+
+def mrt_rates(tau):
+    out = np.zeros(19)
+    _load().or_mrt_rates(float(tau), _dp(out))
+    return out
+
+
+def collide_mrt(f, tau0, cs, F, damp=1.0):
+    """Returns (f*, rho, u, tau_eff) for one cell with the MRT operator."""
+    fs = np.zeros(19)
+    rho = np.zeros(1)
+    u = np.zeros(3)
+    tau = np.zeros(1)
+    _load().or_collide_mrt(_dp(_vec(f, 19)), float(tau0), float(cs), _dp(_vec(F, 3)), float(damp), _dp(fs),
+                           _dp(rho), _dp(u), _dp(tau))
+    return fs, rho[0], u, tau[0]
+
+
+def collide_mrt_rates(f, tau0, cs, F, rates, damp=1.0):
+    fs = np.zeros(19)
+    rho = np.zeros(1)
+    u = np.zeros(3)
+    tau = np.zeros(1)
+    _load().or_collide_mrt_rates(_dp(_vec(f, 19)), float(tau0), float(cs), _dp(_vec(F, 3)), float(damp),
+                                 _dp(_vec(rates, 19)), _dp(fs), _dp(rho), _dp(u), _dp(tau))
+    return fs, rho[0], u, tau[0]
+
+
+def van_driest(j, ny, u_tau, nu, a_plus=26.0):
+    return _load().or_van_driest(int(j), int(ny), float(u_tau), float(nu), float(a_plus))
 
 
 def spalding_yplus(up, kappa=0.41, B=5.5):
@@ -267,3 +310,7 @@ class Lattice:
 
     def step(self, n=1):
         self._lib.or_step(self._h, int(n))
+
+    def set_les(self, collision=0, u_tau=0.0, a_plus=0.0):
+        """collision 0 BGK / 1 MRT; van Driest damping when a_plus > 0."""
+        self._lib.or_set_les(self._h, int(collision), float(u_tau), float(a_plus))

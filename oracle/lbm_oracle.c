@@ -158,6 +158,136 @@ void or_collide(const double *f, double tau0, double cs, const double *F,
     if (tau_out) *tau_out = tau;
 }
 
+/* ------------------------------------------------------- MRT collision -- */
+
+/* Moment basis of the D3Q19 multiple-relaxation-time model of d'Humieres et
+ * al. (2002), the MRT of ref. [40] used in Sec. 3.1. Row i, direction a, with
+ * e = e_a and |e|^2 = e.e:
+ *   0 rho 1                     1 e   19|e|^2 - 30        2 eps (21|e|^4 - 53|e|^2 + 24)/2
+ *   3 j_x e_x                   4 q_x (5|e|^2 - 9) e_x    5 j_y, 6 q_y, 7 j_z, 8 q_z alike
+ *   9 3p_xx 3e_x^2 - |e|^2     10 3pi_xx (3|e|^2 - 5)(3e_x^2 - |e|^2)
+ *  11 p_ww e_y^2 - e_z^2       12 pi_ww (3|e|^2 - 5)(e_y^2 - e_z^2)
+ *  13 p_xy e_x e_y             14 p_yz e_y e_z             15 p_xz e_x e_z
+ *  16 m_x (e_y^2 - e_z^2) e_x  17 m_y (e_z^2 - e_x^2) e_y  18 m_z (e_x^2 - e_y^2) e_z */
+void or_mrt_matrix(double *M)
+{
+    for (int a = 0; a < Q; ++a) {
+        const double x = E[a][0], y = E[a][1], z = E[a][2];
+        const double e2 = x * x + y * y + z * z;
+        double r[Q];
+        r[0] = 1.0;
+        r[1] = 19.0 * e2 - 30.0;
+        r[2] = (21.0 * e2 * e2 - 53.0 * e2 + 24.0) / 2.0;
+        r[3] = x;
+        r[4] = (5.0 * e2 - 9.0) * x;
+        r[5] = y;
+        r[6] = (5.0 * e2 - 9.0) * y;
+        r[7] = z;
+        r[8] = (5.0 * e2 - 9.0) * z;
+        r[9] = 3.0 * x * x - e2;
+        r[10] = (3.0 * e2 - 5.0) * (3.0 * x * x - e2);
+        r[11] = y * y - z * z;
+        r[12] = (3.0 * e2 - 5.0) * (y * y - z * z);
+        r[13] = x * y;
+        r[14] = y * z;
+        r[15] = x * z;
+        r[16] = (y * y - z * z) * x;
+        r[17] = (z * z - x * x) * y;
+        r[18] = (x * x - y * y) * z;
+        for (int i = 0; i < Q; ++i) M[i * Q + a] = r[i];
+    }
+}
+
+/* Relaxation rates of the d'Humieres et al. (2002) D3Q19 model: s_e = 1.19,
+ * s_eps = 1.4, s_q = 1.2, s_pi = 1.4, s_m = 1.98; the five stress moments
+ * (9, 11, 13, 14, 15) relax with 1/tau_eff (viscosity); the conserved moments
+ * (0, 3, 5, 7) take 1 (their value does not enter the result). */
+void or_mrt_rates(double tau, double *s)
+{
+    for (int i = 0; i < Q; ++i) s[i] = 1.0;
+    s[1] = 1.19;
+    s[2] = 1.4;
+    s[4] = s[6] = s[8] = 1.2;
+    s[10] = s[12] = 1.4;
+    s[16] = s[17] = s[18] = 1.98;
+    s[9] = s[11] = s[13] = s[14] = s[15] = 1.0 / tau;
+}
+
+/* One MRT collision with the same moments, equilibrium, Smagorinsky closure
+ * and Guo forcing as or_collide: with m = M f,
+ *   m* = m - S (m - M f^eq) + (I - S/2) M G,  G_a = w_a [3 (e_a - u) + 9 (e_a.u) e_a].F
+ *   f* = M^-1 m*  (M has orthogonal rows: M^-1 = M^T diag(1 / |row|^2)).
+ * `damp` multiplies C_s (van Driest factor, 1 = none). With every rate 1/tau
+ * the update is exactly BGK. */
+void or_collide_mrt_rates(const double *f, double tau0, double cs, const double *F, double damp,
+                          const double *rates, double *fstar, double *rho_out, double *u_out,
+                          double *tau_out);
+
+void or_collide_mrt(const double *f, double tau0, double cs, const double *F, double damp,
+                    double *fstar, double *rho_out, double *u_out, double *tau_out)
+{
+    or_collide_mrt_rates(f, tau0, cs, F, damp, NULL, fstar, rho_out, u_out, tau_out);
+}
+
+/* As or_collide_mrt with the 19 rates given explicitly (rates != NULL). */
+void or_collide_mrt_rates(const double *f, double tau0, double cs, const double *F, double damp,
+                          const double *rates, double *fstar, double *rho_out, double *u_out,
+                          double *tau_out)
+{
+    static double M[Q * Q];
+    static int built = 0;
+    if (!built) {
+        or_mrt_matrix(M);
+        built = 1;
+    }
+    double rho, u[3], feq[Q], pi[9], G[Q], s[Q];
+    or_moments_cell(f, F, &rho, u);
+    or_feq(rho, u, feq);
+    or_pi_neq(f, feq, pi);
+    const double tau = or_tau_eff(tau0, cs * damp, rho, pi);
+    or_mrt_rates(tau, s);
+    if (rates)
+        for (int i = 0; i < Q; ++i) s[i] = rates[i];
+    for (int a = 0; a < Q; ++a) {
+        double eu = E[a][0] * u[0] + E[a][1] * u[1] + E[a][2] * u[2];
+        double t = 0.0;
+        for (int c = 0; c < 3; ++c) t += (3.0 * (E[a][c] - u[c]) + 9.0 * eu * E[a][c]) * F[c];
+        G[a] = weight(a) * t;
+    }
+    double dm[Q];
+    for (int i = 0; i < Q; ++i) {
+        double m = 0.0, meq = 0.0, mg = 0.0;
+        for (int a = 0; a < Q; ++a) {
+            m += M[i * Q + a] * f[a];
+            meq += M[i * Q + a] * feq[a];
+            mg += M[i * Q + a] * G[a];
+        }
+        dm[i] = -s[i] * (m - meq) + (1.0 - 0.5 * s[i]) * mg;
+    }
+    for (int a = 0; a < Q; ++a) {
+        double df = 0.0;
+        for (int i = 0; i < Q; ++i) {
+            double n2 = 0.0;
+            for (int b = 0; b < Q; ++b) n2 += M[i * Q + b] * M[i * Q + b];
+            df += M[i * Q + a] * dm[i] / n2;
+        }
+        fstar[a] = f[a] + df;
+    }
+    if (rho_out) *rho_out = rho;
+    if (u_out) for (int c = 0; c < 3; ++c) u_out[c] = u[c];
+    if (tau_out) *tau_out = tau;
+}
+
+/* van Driest damping factor 1 - exp(-y+ / A+) of the Smagorinsky length for
+ * layer j of ny (halfway walls: the layer centre lies j + 1/2 from the bottom
+ * wall), with y+ = y u_tau / nu from a reference friction velocity. */
+double or_van_driest(int j, int ny, double u_tau, double nu, double a_plus)
+{
+    double d = j + 0.5;
+    if (ny - j - 0.5 < d) d = ny - j - 0.5;
+    return 1.0 - exp(-d * u_tau / nu / a_plus);
+}
+
 /* --------------------------------------------------- Spalding wall law -- */
 
 /* Eq. 16: y+ as an explicit function of u+. */
@@ -244,6 +374,8 @@ typedef struct {
     double tau0, cs, F[3];
     int wall;                   /* 0 bounce-back, 1 WFB, 2 free-slip */
     double kappa, B, y1, nu;
+    int collision;              /* 0 BGK, 1 MRT */
+    double vd_utau, vd_aplus;   /* van Driest reference u_tau and A+ (A+ <= 0: off) */
     double *f, *g;              /* current and next populations [19][n] */
     double *tw;                 /* wall stress of the last step [2][nz][nx][2] */
     double *dfw;                /* Eq. B-1 per wall of the last step [2] */
@@ -383,6 +515,15 @@ long long or_get_step(const or_lattice *L)
     return L->step;
 }
 
+/* Collision operator (0 BGK, 1 MRT) and van Driest damping of the
+ * Smagorinsky length (a_plus <= 0 turns it off). */
+void or_set_les(or_lattice *L, int collision, double u_tau, double a_plus)
+{
+    L->collision = collision;
+    L->vd_utau = u_tau;
+    L->vd_aplus = a_plus;
+}
+
 /* One time step t -> t+1: for every cell collide (Eq. 1), find the wall
  * stress of wall-layer cells, then stream each post-collision population to
  * x + e_a. A population that would cross a wall is
@@ -405,7 +546,12 @@ void or_step(or_lattice *L, int nsteps)
                     long long i = cidx(L, x, y, z);
                     double f[Q], fs[Q], rho, u[3], tau;
                     for (int a = 0; a < Q; ++a) f[a] = L->f[a * n + i];
-                    or_collide(f, L->tau0, L->cs, L->F, fs, &rho, u, &tau);
+                    double damp = 1.0;
+                    if (L->vd_aplus > 0.0) damp = or_van_driest(y, ny, L->vd_utau, L->nu, L->vd_aplus);
+                    if (L->collision == 1)
+                        or_collide_mrt(f, L->tau0, L->cs, L->F, damp, fs, &rho, u, &tau);
+                    else
+                        or_collide(f, L->tau0, L->cs * damp, L->F, fs, &rho, u, &tau);
 
                     int wall_id = (y == 0) ? 0 : ((y == ny - 1) ? 1 : -1);
                     double tw[2] = {0.0, 0.0};

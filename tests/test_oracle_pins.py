@@ -389,3 +389,96 @@ def test_table1_first_layer_convention():
     """y1 = 1 lattice spacing reproduces Table 1's printed first-layer y+."""
     for _case, re_tau, d_over_dx, yplus in _rows("table1_first_layer.txt"):
         assert round(float(re_tau) * 1.0 / float(d_over_dx)) == int(yplus)
+
+
+# ----------------------------------------------------------------------- MRT --
+
+def test_mrt_basis_orthogonal_with_published_norms(oracle_lib):
+    M = oracle_lib.mrt_matrix()
+    G = M @ M.T
+    norms = [float(v) for v in _rows("mrt_d3q19_row_norms.txt")[0]]
+    assert np.array_equal(G, np.diag(np.diag(G)))
+    assert np.allclose(np.diag(G), norms)
+    e, _, _, _ = oracle_lib.table()
+    assert np.array_equal(M[0], np.ones(19))
+    assert np.array_equal(M[3], e[:, 0]) and np.array_equal(M[5], e[:, 1]) and np.array_equal(M[7], e[:, 2])
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_mrt_with_equal_rates_is_bgk(oracle_lib, seed):
+    rng = np.random.default_rng(40 + seed)
+    f = oracle_lib.feq(1.0, 0.05 * rng.random(3)) * (1 + 0.05 * (rng.random(19) - 0.5))
+    F = np.array([2e-6, 1e-6, -3e-6])
+    fb, rho, u, tau = oracle_lib.collide(f, 0.53, 0.1, F)
+    fm, rho2, u2, tau2 = oracle_lib.collide_mrt_rates(f, 0.53, 0.1, F, np.full(19, 1.0 / tau))
+    assert tau2 == tau
+    assert np.allclose(fm, fb, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_mrt_conserves_mass_and_adds_force(oracle_lib, seed):
+    e, _, _, _ = oracle_lib.table()
+    rng = np.random.default_rng(50 + seed)
+    f = oracle_lib.feq(1.0, 0.05 * rng.random(3)) * (1 + 0.05 * (rng.random(19) - 0.5))
+    F = np.array([3e-6, -1e-6, 2e-6])
+    fs, rho, u, tau = oracle_lib.collide_mrt(f, 0.52, 0.1, F)
+    assert abs(fs.sum() - f.sum()) < 1e-15
+    assert np.allclose(e.T @ (fs - f), F, rtol=1e-8, atol=1e-17)
+    # the ghost moments relax toward their equilibria with the published rates
+    M = oracle_lib.mrt_matrix()
+    s = oracle_lib.mrt_rates(tau)
+    assert s[1] == 1.19 and s[2] == 1.4 and s[4] == 1.2 and s[16] == 1.98 and s[9] == 1.0 / tau
+
+
+def _shear_wave_decay(oracle_lib, collision, tau, nz=64, steps=400, amp=1e-3):
+    L = oracle_lib.Lattice(1, 2, nz, tau, 0.0, (0, 0, 0), 2)
+    L.set_les(collision)
+    z = np.arange(nz)
+    f = np.stack([oracle_lib.feq(1.0, [amp * math.sin(2 * math.pi * k / nz), 0, 0]) for k in z], axis=1)
+    L.set_populations(np.repeat(f[:, :, None], 2, axis=2).reshape(19, -1))
+    L.step(steps)
+    _, u = L.moments()
+    a = 2.0 / nz * np.sum(u[0, :, 0, 0] * np.sin(2 * math.pi * z / nz))
+    return a / amp
+
+
+@pytest.mark.parametrize("tau", [0.6, 0.9])
+def test_mrt_shear_wave_viscosity(oracle_lib, tau):
+    """A shear wave decays as exp(-nu k^2 t) with nu = (tau - 1/2)/3 set by the
+    stress-moment rate; MRT and BGK agree to O(k^2) (the ghost rates enter only
+    at higher order in k)."""
+    nz, steps = 64, 400
+    nu = (tau - 0.5) / 3.0
+    k = 2 * math.pi / nz
+    expect = math.exp(-nu * k * k * steps)
+    mrt = _shear_wave_decay(oracle_lib, 1, tau, nz, steps)
+    bgk = _shear_wave_decay(oracle_lib, 0, tau, nz, steps)
+    assert mrt == pytest.approx(expect, rel=2e-3)
+    assert mrt == pytest.approx(bgk, rel=1e-3)
+
+
+def test_van_driest_limits(oracle_lib):
+    """1 - exp(-y+/A+): linear near the wall, 1 - 1/e at y+ = A+, -> 1 far away;
+    layer centres lie j + 1/2 from the nearer wall."""
+    nu, ut = 1e-3, 1e-3                      # y+ = y
+    assert oracle_lib.van_driest(0, 200, ut, nu, 26.0) == pytest.approx(1 - math.exp(-0.5 / 26.0))
+    assert oracle_lib.van_driest(199, 200, ut, nu, 26.0) == oracle_lib.van_driest(0, 200, ut, nu, 26.0)
+    j = 25                                   # y = 25.5
+    assert oracle_lib.van_driest(j, 200, ut, nu, 25.5) == pytest.approx(1 - math.exp(-1.0))
+    assert oracle_lib.van_driest(99, 200, ut, nu, 26.0) > 0.97
+
+
+def test_mrt_smagorinsky_with_damping(oracle_lib):
+    """The damped Smagorinsky length C_s D gives tau_eff of a Chapman-Enskog cell
+    built for C_s' = C_s D (same closure as BGK)."""
+    rng = np.random.default_rng(61)
+    A = 1e-3 * (rng.random((3, 3)) - 0.5)
+    S = 0.5 * (A + A.T)
+    S -= np.trace(S) / 3.0 * np.eye(3)
+    tau0, tau_t = 0.52, 0.61
+    smag = math.sqrt(2.0 * float(np.sum(S * S)))
+    cs_eff = math.sqrt((tau_t - tau0) / 3.0 / smag)
+    damp = 0.7
+    f = _chapman_enskog_f(oracle_lib, 1.0, np.zeros(3), S, tau_t)
+    _, _, _, tau = oracle_lib.collide_mrt(f, tau0, cs_eff / damp, np.zeros(3), damp)
+    assert abs(tau - tau_t) < 1e-12
