@@ -157,6 +157,21 @@ int lbm_set_kernel(lbm_handle *h, int kernel);
 /* The kernel form in use (never LBM_KERNEL_AUTO), -1 for a NULL handle. */
 int lbm_get_kernel(lbm_handle *h);
 
+typedef enum {
+    LBM_COLLISION_BGK = 0,  /* single relaxation time (default) */
+    LBM_COLLISION_MRT = 1   /* D3Q19 multiple relaxation times (ref. [40] of Sec. 3.1) */
+} lbm_collision;
+
+/* LES model (Sec. 3.1). collision: BGK, or the D3Q19 MRT of d'Humieres et al.
+ * (2002) (moments rho, e, eps, j, q, 3p_xx, 3pi_xx, p_ww, pi_ww, p_xy, p_yz,
+ * p_xz, m; ghost rates 1.19, 1.4, 1.2, 1.4, 1.98; the five stress moments relax
+ * with 1/tau_eff; equilibrium moments M f^eq; Guo forcing in moment space).
+ * Both use the Smagorinsky tau_eff. u_tau_ref > 0 and a_plus > 0 add van Driest
+ * damping of the Smagorinsky length, C_s (1 - exp(-y+/A+)), with y the layer
+ * centre's distance to the nearer wall (j + 1/2) and y+ = y u_tau_ref / nu (nu
+ * of the wall model); both 0 turn it off. Synchronises; keeps the state. */
+int lbm_set_les(lbm_handle *h, int collision, double u_tau_ref, double a_plus);
+
 /* Density rho [nz][ny][nx] and velocity u [3][nz][ny][nx] of the current
  * populations (Eq. 2 with the Guo half-force shift, u = (sum e f + F/2)/rho),
  * FP32. on_device != 0: rho and u are device pointers and the call is
@@ -251,6 +266,10 @@ int lbm_batch_step(lbm_batch *b, int n);
  * row) and CTAs per SM (<= 0 or above the occupancy limit selects the limit). */
 int lbm_batch_set_config(lbm_batch *b, int threads, int ctas_per_sm);
 int lbm_batch_get_config(lbm_batch *b, int *threads, int *ctas_per_sm, int *grid, long long *tiles);
+
+/* LES model of every member (see lbm_set_les): one collision operator for the
+ * batch; u_tau_ref [n] (host, may be NULL: no damping) per member and a_plus. */
+int lbm_batch_set_les(lbm_batch *b, int collision, const double *u_tau_ref, double a_plus);
 
 /* Time every launch shape for `steps` steps (after 2 warm-up steps) and keep
  * the fastest; best_ms (nullable) receives its time per step. The timed steps

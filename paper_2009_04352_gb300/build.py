@@ -1,6 +1,7 @@
 """Build the CUDA library in-tree with nvcc for sm_103a (GB300)."""
 from __future__ import annotations
 
+import concurrent.futures
 import os
 import subprocess
 
@@ -36,12 +37,20 @@ def build(force: bool = False, verbose: bool = False) -> str:
     tmp = LIB + f".tmp{os.getpid()}"
     # approximate FP32 division and square root (2 ulp): the relaxation time and
     # velocity tolerate it, and IEEE-exact forms cost ~4x the instructions
-    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-prec-div=false", "-prec-sqrt=false",
-           "-Xcompiler", "-fPIC", "-shared",
-           "-I" + os.path.join(ROOT, "include"), "-o", tmp, *srcs]
+    flags = [*ARCH, "-O3", "-lineinfo", "-std=c++17", "-prec-div=false", "-prec-sqrt=false",
+             "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include")]
     if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-    subprocess.run(cmd, check=True)
+        flags.append("-Xptxas=-v")
+    objs = [os.path.join(BUILD, os.path.splitext(os.path.basename(s))[0] + f".{os.getpid()}.o") for s in srcs]
+    # one nvcc per translation unit, in parallel
+    with concurrent.futures.ThreadPoolExecutor(max_workers=len(srcs)) as pool:
+        jobs = [pool.submit(subprocess.run, [nvcc(), *flags, "-c", "-o", o, src], check=True)
+                for src, o in zip(srcs, objs)]
+        for j in jobs:
+            j.result()
+    subprocess.run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs], check=True)
+    for o in objs:
+        os.remove(o)
     os.replace(tmp, LIB)
     return LIB
 

@@ -103,47 +103,65 @@ long long partials_per_plane(const lbm_handle *h)
     return (long long)step_grid(h).x * h->g.nz;
 }
 
-template <typename T, int NW>
+// Launch with programmatic stream serialisation (see pdl_begin in lbm_pair.cuh).
+template <typename... K, typename... A>
+cudaError_t launch_pdl(void (*kernel)(K...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+template <typename T, int NW, int COLL>
 void launch_rows_t(lbm_handle *h, cudaStream_t s, int src, bool stats)
 {
     const T *a = (const T *)h->f[src];
     T *b = (T *)h->f[src ^ 1];
     const dim3 grid(h->tma_grid), block(NW * 32);
     if (stats)
-        lbm::k_step_rows<T, true, NW><<<grid, block, h->tma_smem, s>>>(a, b, h->g, h->p, h->tw, h->part, h->err,
-                                                                        h->tma_stages);
+        lbm::k_step_rows<T, true, NW, COLL><<<grid, block, h->tma_smem, s>>>(a, b, h->g, h->p, h->tw, h->part, h->err,
+                                                                              h->tma_stages);
     else
-        lbm::k_step_rows<T, false, NW><<<grid, block, h->tma_smem, s>>>(a, b, h->g, h->p, h->tw, h->part, h->err,
-                                                                         h->tma_stages);
-}
-
-int launch_tma(lbm_handle *h, cudaStream_t s, int src, bool stats)
-{
-    if (h->precision == LBM_FP16_SHIFTED) {
-        if (h->tma_warps == 8)
-            launch_rows_t<__half, 8>(h, s, src, stats);
-        else
-            launch_rows_t<__half, 4>(h, s, src, stats);
-    } else {
-        if (h->tma_warps == 8)
-            launch_rows_t<float, 8>(h, s, src, stats);
-        else
-            launch_rows_t<float, 4>(h, s, src, stats);
-    }
-    return LBM_OK;
+        lbm::k_step_rows<T, false, NW, COLL><<<grid, block, h->tma_smem, s>>>(a, b, h->g, h->p, h->tw, h->part,
+                                                                               h->err, h->tma_stages);
 }
 
 // Blocks per SM of one row-kernel instantiation with `smem` dynamic bytes.
-template <typename T, int NW>
-int rows_occupancy(int smem, int *per_sm)
+template <typename T, int NW, int COLL>
+int rows_occupancy_c(int smem, int *per_sm)
 {
-    CK(cudaFuncSetAttribute(lbm::k_step_rows<T, false, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    CK(cudaFuncSetAttribute(lbm::k_step_rows<T, true, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, lbm::k_step_rows<T, false, NW>, NW * 32, smem));
+    CK(cudaFuncSetAttribute(lbm::k_step_rows<T, false, NW, COLL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    CK(cudaFuncSetAttribute(lbm::k_step_rows<T, true, NW, COLL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, lbm::k_step_rows<T, false, NW, COLL>, NW * 32, smem));
     int st = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&st, lbm::k_step_rows<T, true, NW>, NW * 32, smem));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&st, lbm::k_step_rows<T, true, NW, COLL>, NW * 32, smem));
     *per_sm = std::min(*per_sm, st);
     return LBM_OK;
+}
+
+int rows_occupancy(const lbm_handle *h, int nw, int smem, int *per_sm)
+{
+    const bool half = h->precision == LBM_FP16_SHIFTED, mrt = h->p.collision == lbm::COLL_MRT;
+    if (half) {
+        if (mrt)
+            return nw == 8 ? rows_occupancy_c<__half, 8, lbm::COLL_MRT>(smem, per_sm)
+                           : rows_occupancy_c<__half, 4, lbm::COLL_MRT>(smem, per_sm);
+        return nw == 8 ? rows_occupancy_c<__half, 8, lbm::COLL_BGK>(smem, per_sm)
+                       : rows_occupancy_c<__half, 4, lbm::COLL_BGK>(smem, per_sm);
+    }
+    if (mrt)
+        return nw == 8 ? rows_occupancy_c<float, 8, lbm::COLL_MRT>(smem, per_sm)
+                       : rows_occupancy_c<float, 4, lbm::COLL_MRT>(smem, per_sm);
+    return nw == 8 ? rows_occupancy_c<float, 8, lbm::COLL_BGK>(smem, per_sm)
+                   : rows_occupancy_c<float, 4, lbm::COLL_BGK>(smem, per_sm);
 }
 
 // Warps per CTA, ring depth and grid of the row kernel: the most resident
@@ -161,11 +179,8 @@ int configure_rows(lbm_handle *h)
         const int smem = half ? lbm::rows_smem_bytes<__half>(h->g.nx, stages)
                               : lbm::rows_smem_bytes<float>(h->g.nx, stages);
         if (smem > smem_max) continue;
-        int per_sm = 0, rc;
-        if (half)
-            rc = nw == 8 ? rows_occupancy<__half, 8>(smem, &per_sm) : rows_occupancy<__half, 4>(smem, &per_sm);
-        else
-            rc = nw == 8 ? rows_occupancy<float, 8>(smem, &per_sm) : rows_occupancy<float, 4>(smem, &per_sm);
+        int per_sm = 0;
+        const int rc = rows_occupancy(h, nw, smem, &per_sm);
         if (rc != LBM_OK) return rc;
         if (per_sm * nw > best_warps) {
             best_warps = per_sm * nw;
@@ -180,79 +195,68 @@ int configure_rows(lbm_handle *h)
                        : lbm::rows_smem_bytes<float>(h->g.nx, best_stages);
     h->tma_grid = sms * best_per_sm;
     // the probe above left the attribute at the last candidate: set the chosen size
-    int per_sm = 0, rc;
-    if (half)
-        rc = nw == 8 ? rows_occupancy<__half, 8>(h->tma_smem, &per_sm) : rows_occupancy<__half, 4>(h->tma_smem, &per_sm);
-    else
-        rc = nw == 8 ? rows_occupancy<float, 8>(h->tma_smem, &per_sm) : rows_occupancy<float, 4>(h->tma_smem, &per_sm);
-    return rc;
+    int per_sm = 0;
+    return rows_occupancy(h, nw, h->tma_smem, &per_sm);
 }
 
-// Two-cell step launched with programmatic stream serialisation (see pdl_begin).
-template <typename T, bool STATS>
-cudaError_t launch_pair_pdl(lbm_handle *h, cudaStream_t s, dim3 grid, dim3 block, const void *a, void *b)
-{
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, lbm::k_step_pair<T, STATS>, (const T *)a, (T *)b, h->g, h->p, h->tw, h->part);
-}
-
-template <bool STATS>
-cudaError_t launch_quad_pdl(lbm_handle *h, cudaStream_t s, dim3 grid, dim3 block, const void *a, void *b)
-{
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, lbm::k_step_quad<STATS>, (const __half *)a, (__half *)b, h->g, h->p, h->tw,
-                              h->part);
-}
-
-int launch_step(lbm_handle *h, cudaStream_t s, int src, bool stats)
+// One step with the kernel form of the handle, collision operator COLL.
+template <int COLL>
+int launch_step_c(lbm_handle *h, cudaStream_t s, int src, bool stats)
 {
     const dim3 grid = step_grid(h), block(h->bx);
+    const bool half = h->precision == LBM_FP16_SHIFTED;
     const void *a = h->f[src];
     void *b = h->f[src ^ 1];
+    cudaError_t e = cudaSuccess;
     if (h->kernel == LBM_KERNEL_TMA) {
-        launch_tma(h, s, src, stats);
+        if (half) {
+            if (h->tma_warps == 8)
+                launch_rows_t<__half, 8, COLL>(h, s, src, stats);
+            else
+                launch_rows_t<__half, 4, COLL>(h, s, src, stats);
+        } else {
+            if (h->tma_warps == 8)
+                launch_rows_t<float, 8, COLL>(h, s, src, stats);
+            else
+                launch_rows_t<float, 4, COLL>(h, s, src, stats);
+        }
     } else if (h->kernel == LBM_KERNEL_QUAD) {
-        const cudaError_t e = stats ? launch_quad_pdl<true>(h, s, grid, block, a, b)
-                                    : launch_quad_pdl<false>(h, s, grid, block, a, b);
-        if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "step launch: %s", cudaGetErrorString(e));
+        const __half *ah = (const __half *)a;
+        __half *bh = (__half *)b;
+        e = stats ? launch_pdl(lbm::k_step_quad<true, COLL>, grid, block, 0, s, ah, bh, h->g, h->p, h->tw, h->part)
+                  : launch_pdl(lbm::k_step_quad<false, COLL>, grid, block, 0, s, ah, bh, h->g, h->p, h->tw, h->part);
     } else if (h->kernel == LBM_KERNEL_PAIR) {
-        cudaError_t e;
-        if (h->precision == LBM_FP16_SHIFTED)
-            e = stats ? launch_pair_pdl<__half, true>(h, s, grid, block, a, b)
-                      : launch_pair_pdl<__half, false>(h, s, grid, block, a, b);
-        else
-            e = stats ? launch_pair_pdl<float, true>(h, s, grid, block, a, b)
-                      : launch_pair_pdl<float, false>(h, s, grid, block, a, b);
-        if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "step launch: %s", cudaGetErrorString(e));
-    } else if (h->precision == LBM_FP16_SHIFTED) {
+        if (half) {
+            const __half *ah = (const __half *)a;
+            __half *bh = (__half *)b;
+            e = stats ? launch_pdl(lbm::k_step_pair<__half, true, COLL>, grid, block, 0, s, ah, bh, h->g, h->p, h->tw,
+                                   h->part)
+                      : launch_pdl(lbm::k_step_pair<__half, false, COLL>, grid, block, 0, s, ah, bh, h->g, h->p, h->tw,
+                                   h->part);
+        } else {
+            const float *af = (const float *)a;
+            float *bf = (float *)b;
+            e = stats ? launch_pdl(lbm::k_step_pair<float, true, COLL>, grid, block, 0, s, af, bf, h->g, h->p, h->tw,
+                                   h->part)
+                      : launch_pdl(lbm::k_step_pair<float, false, COLL>, grid, block, 0, s, af, bf, h->g, h->p, h->tw,
+                                   h->part);
+        }
+    } else if (half) {
         if (stats)
-            lbm::k_step<__half, true><<<grid, block, 0, s>>>((const __half *)a, (__half *)b, h->g, h->p, h->tw, h->part);
+            lbm::k_step<__half, true, COLL><<<grid, block, 0, s>>>((const __half *)a, (__half *)b, h->g, h->p, h->tw,
+                                                                   h->part);
         else
-            lbm::k_step<__half, false><<<grid, block, 0, s>>>((const __half *)a, (__half *)b, h->g, h->p, h->tw, h->part);
+            lbm::k_step<__half, false, COLL><<<grid, block, 0, s>>>((const __half *)a, (__half *)b, h->g, h->p, h->tw,
+                                                                    h->part);
     } else {
         if (stats)
-            lbm::k_step<float, true><<<grid, block, 0, s>>>((const float *)a, (float *)b, h->g, h->p, h->tw, h->part);
+            lbm::k_step<float, true, COLL><<<grid, block, 0, s>>>((const float *)a, (float *)b, h->g, h->p, h->tw,
+                                                                  h->part);
         else
-            lbm::k_step<float, false><<<grid, block, 0, s>>>((const float *)a, (float *)b, h->g, h->p, h->tw, h->part);
+            lbm::k_step<float, false, COLL><<<grid, block, 0, s>>>((const float *)a, (float *)b, h->g, h->p, h->tw,
+                                                                   h->part);
     }
+    if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "step launch: %s", cudaGetErrorString(e));
     CK_LAUNCH();
     if (stats) {
         const long long per_plane = partials_per_plane(h);
@@ -261,6 +265,12 @@ int launch_step(lbm_handle *h, cudaStream_t s, int src, bool stats)
         CK_LAUNCH();
     }
     return LBM_OK;
+}
+
+int launch_step(lbm_handle *h, cudaStream_t s, int src, bool stats)
+{
+    return h->p.collision == lbm::COLL_MRT ? launch_step_c<lbm::COLL_MRT>(h, s, src, stats)
+                                           : launch_step_c<lbm::COLL_BGK>(h, s, src, stats);
 }
 
 int build_chunk(lbm_handle *h, int start)
@@ -368,6 +378,30 @@ int lbm_create_handle(lbm_grid g, double tau, double C_s, const double force[3],
         h->p.weF[k] = (float)(lbm::w_of(a) * eF);
     }
     h->p.t02 = (float)((double)h->p.tau0 * (double)h->p.tau0);
+    h->nu_wall = nu;
+    // MRT constants: ghost rates of d'Humieres et al. (2002) and the Guo
+    // forcing in moment space, M G = gc + gu . u with
+    // G_a = w_a [3 e_a.F + (9 (e_a.u)(e_a.F) - 3 u.F)]
+    h->p.collision = lbm::COLL_BGK;
+    h->p.vd_scale = 0.f;
+    for (int i = 0; i < lbm::Q; ++i) {
+        double r = 1.0;
+        if (i == 1) r = 1.19;
+        if (i == 2 || i == 10 || i == 12) r = 1.4;
+        if (i == 4 || i == 6 || i == 8) r = 1.2;
+        if (i >= 16) r = 1.98;
+        h->p.mrt_s[i] = (float)r;
+        double gc = 0.0, gu[3] = {0.0, 0.0, 0.0};
+        for (int a = 0; a < lbm::Q; ++a) {
+            const int e[3] = {lbm::ex_of(a), lbm::ey_of(a), lbm::ez_of(a)};
+            const double eF = e[0] * force[0] + e[1] * force[1] + e[2] * force[2];
+            const double w = lbm::w_of(a), c = lbm::mrt_coef(i, a);
+            gc += c * 3.0 * w * eF;
+            for (int al = 0; al < 3; ++al) gu[al] += c * w * (9.0 * e[al] * eF - 3.0 * force[al]);
+        }
+        h->p.mrt_gc[i] = (float)gc;
+        for (int al = 0; al < 3; ++al) h->p.mrt_gu[i][al] = (float)gu[al];
+    }
     h->precision = precision;
     h->layout = layout;
     h->stream = (cudaStream_t)cuda_stream;
@@ -414,6 +448,16 @@ int lbm_create_handle(lbm_grid g, double tau, double C_s, const double force[3],
     rc = ensure_part(h, nblk * lbm::K_PART);
     if (rc != LBM_OK) return bail(rc);
     *out = h;
+    return LBM_OK;
+}
+
+int lbm_apply_les(lbm_handle *h, int collision, double u_tau, double a_plus)
+{
+    if (collision != lbm::COLL_BGK && collision != lbm::COLL_MRT) return fail(LBM_ERR_ARG, "unknown collision");
+    if (!(u_tau >= 0.0) || !(a_plus >= 0.0) || (u_tau > 0.0) != (a_plus > 0.0))
+        return fail(LBM_ERR_ARG, "van Driest needs both u_tau > 0 and A+ > 0 (or both 0)");
+    h->p.collision = collision;
+    h->p.vd_scale = a_plus > 0.0 ? (float)(u_tau / (h->nu_wall * a_plus)) : 0.f;
     return LBM_OK;
 }
 
@@ -555,6 +599,16 @@ int lbm_set_kernel(lbm_handle *h, int kernel)
 }
 
 int lbm_get_kernel(lbm_handle *h) { return h ? h->kernel : -1; }
+
+int lbm_set_les(lbm_handle *h, int collision, double u_tau_ref, double a_plus)
+{
+    if (!h) return fail(LBM_ERR_ARG, "NULL handle");
+    if (h->member) return fail(LBM_ERR_STATE, "set the LES model of a batch with lbm_batch_set_les");
+    CK(cudaStreamSynchronize(h->stream));
+    const int rc = lbm_apply_les(h, collision, u_tau_ref, a_plus);
+    if (rc != LBM_OK) return rc;
+    return select_kernel(h, h->kernel);   // launch shapes and graphs depend on the operator
+}
 
 int lbm_moments(lbm_handle *h, float *rho, float *u, int on_device)
 {

@@ -42,7 +42,7 @@ struct BatchInst {
 #define LBM_BATCH_MIN_BLOCKS 5   // resident CTAs per SM the register budget must allow
 #endif
 
-template <typename T, bool STATS>
+template <typename T, bool STATS, int COLL>
 __global__ void __launch_bounds__(128, LBM_BATCH_MIN_BLOCKS) k_batch_step(const BatchInst *__restrict__ inst, int n, long long total,
                                                     T *__restrict__ pool, int cur)
 {
@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(128, LBM_BATCH_MIN_BLOCKS) k_batch_step(const 
     }
     for (;;) {
         double *part = STATS ? s.part + (((long long)y * s.g.nz + z) * s.nxb + xb) * lbm::K_PART : nullptr;
-        lbm::pair_tile<T, STATS>(pool + s.off[cur], pool + s.off[cur ^ 1], s.g, s.p, s.tw, part, xb, y, z);
+        lbm::pair_tile<T, STATS, COLL>(pool + s.off[cur], pool + s.off[cur ^ 1], s.g, s.p, s.tw, part, xb, y, z);
         if (++t >= t1) break;
         if (++xb == s.nxb) {
             xb = 0;
@@ -145,18 +145,22 @@ void drop_graphs(lbm_batch *b)
         }
 }
 
-int max_ctas_per_sm(const lbm_batch *b, int threads, int *out)
+template <typename T, int COLL>
+int occupancy_c(int threads, int *out)
 {
     int per_sm = 0, st = 0;
-    if (b->precision == LBM_FP16_SHIFTED) {
-        BK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_step<__half, false>, threads, 0));
-        BK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&st, k_batch_step<__half, true>, threads, 0));
-    } else {
-        BK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_step<float, false>, threads, 0));
-        BK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&st, k_batch_step<float, true>, threads, 0));
-    }
+    BK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_step<T, false, COLL>, threads, 0));
+    BK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&st, k_batch_step<T, true, COLL>, threads, 0));
     *out = std::min(per_sm, st);
     return LBM_OK;
+}
+
+int max_ctas_per_sm(const lbm_batch *b, int threads, int *out)
+{
+    const bool mrt = b->members[0]->p.collision == lbm::COLL_MRT;
+    if (b->precision == LBM_FP16_SHIFTED)
+        return mrt ? occupancy_c<__half, lbm::COLL_MRT>(threads, out) : occupancy_c<__half, lbm::COLL_BGK>(threads, out);
+    return mrt ? occupancy_c<float, lbm::COLL_MRT>(threads, out) : occupancy_c<float, lbm::COLL_BGK>(threads, out);
 }
 
 // Rebuild the descriptor table for `threads` per CTA and size the grid.
@@ -193,7 +197,7 @@ int configure(lbm_batch *b, int threads, int ctas_per_sm)
     return LBM_OK;
 }
 
-template <typename T, bool STATS>
+template <typename T, bool STATS, int COLL>
 cudaError_t launch_pdl(lbm_batch *b, cudaStream_t s, int cur)
 {
     cudaLaunchConfig_t cfg = {};
@@ -206,17 +210,25 @@ cudaError_t launch_pdl(lbm_batch *b, cudaStream_t s, int cur)
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_batch_step<T, STATS>, (const BatchInst *)b->d_inst, b->n, b->tiles,
+    return cudaLaunchKernelEx(&cfg, k_batch_step<T, STATS, COLL>, (const BatchInst *)b->d_inst, b->n, b->tiles,
                               (T *)b->pool, cur);
 }
 
 int launch(lbm_batch *b, cudaStream_t s, int cur, bool stats)
 {
     cudaError_t e;
-    if (b->precision == LBM_FP16_SHIFTED)
-        e = stats ? launch_pdl<__half, true>(b, s, cur) : launch_pdl<__half, false>(b, s, cur);
-    else
-        e = stats ? launch_pdl<float, true>(b, s, cur) : launch_pdl<float, false>(b, s, cur);
+    const bool mrt = b->members[0]->p.collision == lbm::COLL_MRT;
+    if (b->precision == LBM_FP16_SHIFTED) {
+        if (mrt)
+            e = stats ? launch_pdl<__half, true, lbm::COLL_MRT>(b, s, cur) : launch_pdl<__half, false, lbm::COLL_MRT>(b, s, cur);
+        else
+            e = stats ? launch_pdl<__half, true, lbm::COLL_BGK>(b, s, cur) : launch_pdl<__half, false, lbm::COLL_BGK>(b, s, cur);
+    } else {
+        if (mrt)
+            e = stats ? launch_pdl<float, true, lbm::COLL_MRT>(b, s, cur) : launch_pdl<float, false, lbm::COLL_MRT>(b, s, cur);
+        else
+            e = stats ? launch_pdl<float, true, lbm::COLL_BGK>(b, s, cur) : launch_pdl<float, false, lbm::COLL_BGK>(b, s, cur);
+    }
     if (e != cudaSuccess) return fail_cuda(e, "batch step launch");
     if (stats) {
         for (int i = 0; i < b->n; ++i) {
@@ -442,6 +454,18 @@ int lbm_batch_autotune(lbm_batch *b, int steps, double *best_ms)
     b->stats_every = saved_stats;
     if (best_ms) *best_ms = best / steps;
     return configure(b, best_t, best_c);
+}
+
+int lbm_batch_set_les(lbm_batch *b, int collision, const double *u_tau_ref, double a_plus)
+{
+    if (!b) return fail(LBM_ERR_ARG, "NULL batch");
+    BK(cudaStreamSynchronize(b->stream));
+    for (int i = 0; i < b->n; ++i) {
+        const double ut = u_tau_ref ? u_tau_ref[i] : 0.0;
+        const int rc = lbm_apply_les(b->members[i], collision, ut, ut > 0.0 ? a_plus : 0.0);
+        if (rc != LBM_OK) return rc;
+    }
+    return configure(b, b->threads, b->ctas_per_sm);   // descriptors carry the physics
 }
 
 int lbm_batch_sync(lbm_batch *b)

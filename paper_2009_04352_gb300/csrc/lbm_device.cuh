@@ -74,7 +74,69 @@ struct Phys {
     float hF[3];         // F / 2
     float weF[9];        // w_k (e_k . F) for the opposite pairs k = 0..8 (directions 2k+1, 2k+2)
     float t02;           // tau0^2
+    // LES model
+    int collision;       // COLL_BGK or COLL_MRT
+    float vd_scale;      // van Driest: u_tau / (nu A+); 0 = no damping
+    float mrt_s[19];     // MRT rates of the ghost moments (stress moments relax with 1/tau_eff)
+    float mrt_gc[19];    // Guo forcing in moment space, M G = gc + gu . u
+    float mrt_gu[19][3];
 };
+
+enum { COLL_BGK = 0, COLL_MRT = 1 };
+
+// Row i, direction a of the D3Q19 MRT moment basis of d'Humieres et al. (2002)
+// (rho, e, eps, j_x, q_x, j_y, q_y, j_z, q_z, 3p_xx, 3pi_xx, p_ww, pi_ww,
+// p_xy, p_yz, p_xz, m_x, m_y, m_z), evaluated at compile time.
+__host__ __device__ constexpr int mrt_coef(int i, int a)
+{
+    const int x = ex_of(a), y = ey_of(a), z = ez_of(a);
+    const int e2 = x * x + y * y + z * z;
+    switch (i) {
+    case 0: return 1;
+    case 1: return 19 * e2 - 30;
+    case 2: return (21 * e2 * e2 - 53 * e2 + 24) / 2;
+    case 3: return x;
+    case 4: return (5 * e2 - 9) * x;
+    case 5: return y;
+    case 6: return (5 * e2 - 9) * y;
+    case 7: return z;
+    case 8: return (5 * e2 - 9) * z;
+    case 9: return 3 * x * x - e2;
+    case 10: return (3 * e2 - 5) * (3 * x * x - e2);
+    case 11: return y * y - z * z;
+    case 12: return (3 * e2 - 5) * (y * y - z * z);
+    case 13: return x * y;
+    case 14: return y * z;
+    case 15: return x * z;
+    case 16: return (y * y - z * z) * x;
+    case 17: return (z * z - x * x) * y;
+    default: return (x * x - y * y) * z;
+    }
+}
+
+// Squared norm of basis row i (the rows are orthogonal: M^-1 = M^T / norm).
+__host__ __device__ constexpr int mrt_norm(int i)
+{
+    int n = 0;
+    for (int a = 0; a < Q; ++a) n += mrt_coef(i, a) * mrt_coef(i, a);
+    return n;
+}
+
+// Moments relaxed with 1/tau_eff (the viscous stress: 3p_xx, p_ww, p_xy, p_yz, p_xz).
+__host__ __device__ constexpr bool mrt_stress(int i) { return i == 9 || i == 11 || i == 13 || i == 14 || i == 15; }
+// Non-conserved moments even (odd) under e -> -e.
+__host__ __device__ constexpr bool mrt_even_ghost(int i) { return i == 1 || i == 2 || (i >= 9 && i <= 15); }
+__host__ __device__ constexpr bool mrt_odd_ghost(int i) { return i == 4 || i == 6 || i == 8 || i >= 16; }
+
+// Smagorinsky coefficient of layer y with the van Driest factor
+// D = 1 - exp(-y+/A+) of the layer centre (j + 1/2 from the nearer wall).
+__device__ __forceinline__ float row_smag(const Phys &p, int y, int ny)
+{
+    if (p.vd_scale <= 0.f) return p.smag;
+    const float d = fminf(y + 0.5f, ny - y - 0.5f);
+    const float D = 1.f - expf(-d * p.vd_scale);
+    return p.smag * D * D;
+}
 
 template <typename T> __device__ __forceinline__ float ld(const T *p);
 template <> __device__ __forceinline__ float ld<float>(const float *p) { return __ldg(p); }

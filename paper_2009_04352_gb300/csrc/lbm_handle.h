@@ -33,7 +33,12 @@ struct lbm_handle {
     int *err;                    // device flag set by a timed-out pipeline wait
     cudaGraphExec_t chunk[2];    // kGraphSteps plain steps starting from cur = 0 / 1
     bool member;                 // member view of a batch: populations owned by the batch
+    double nu_wall;              // viscosity of the wall law and of the van Driest y+
 };
+
+// Set the LES model of a handle's physics: collision (COLL_BGK / COLL_MRT)
+// and the van Driest factor (u_tau > 0 and a_plus > 0, else no damping).
+int lbm_apply_les(lbm_handle *h, int collision, double u_tau, double a_plus);
 
 // Create a handle; with pop0/pop1 non-NULL it is a member view whose two
 // lattices live in a batch pool (nothing is allocated for them).

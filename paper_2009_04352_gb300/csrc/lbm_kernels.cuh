@@ -40,7 +40,8 @@ __device__ __forceinline__ CellState velocity(const Moments &m, const Phys &p)
     return c;
 }
 
-__device__ __forceinline__ CellState collide(const float (&f)[Q], float (&fs)[Q], const Phys &p)
+template <int COLL = COLL_BGK>
+__device__ __forceinline__ CellState collide(const float (&f)[Q], float (&fs)[Q], const Phys &p, float smag)
 {
     const Moments m = moments_of(f);
     const CellState c = velocity(m, p);
@@ -64,12 +65,58 @@ __device__ __forceinline__ CellState collide(const float (&f)[Q], float (&fs)[Q]
     // positive root of tau^2 - tau0 tau - smag Q / (4 rho) = 0, written as
     // tau0 + (root - tau0) so that a small eddy viscosity is not lost to
     // cancellation against tau0
-    const float cq = p.smag * sqrtf(q2) / rho;
+    const float cq = smag * sqrtf(q2) / rho;
     const float tau = p.tau0 + cq / (2.f * (sqrtf(p.tau0 * p.tau0 + cq) + p.tau0));
     const float omega = 1.f / tau;
     const float gk = 1.f - 0.5f * omega;
 
     const float usq = ux * ux + uy * uy + uz * uz;
+    if constexpr (COLL == COLL_MRT) {
+        // MRT (d'Humieres et al. 2002): ghost and stress moments of f - f^eq
+        // relax with their rates; Guo forcing in moment space (gc + gu . u)
+        float n[Q];
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            const float eu = ex_of(a) * ux + ey_of(a) * uy + ez_of(a) * uz;
+            n[a] = f[a] - (float)w_of(a) * (m.drho + rho * (3.f * eu + 4.5f * eu * eu - 1.5f * usq));
+        }
+        float dm[Q];
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            dm[i] = 0.f;
+            if (!mrt_even_ghost(i) && !mrt_odd_ghost(i)) continue;
+            float mi = 0.f;
+#pragma unroll
+            for (int a = 0; a < Q; ++a)
+                if (mrt_coef(i, a) != 0) mi += (float)mrt_coef(i, a) * n[a];
+            const float g = p.mrt_gc[i] + p.mrt_gu[i][0] * ux + p.mrt_gu[i][1] * uy + p.mrt_gu[i][2] * uz;
+            const float sr = mrt_stress(i) ? omega : p.mrt_s[i];
+            dm[i] = (-sr * mi + (1.f - 0.5f * sr) * g) / (float)mrt_norm(i);
+        }
+        float mass = 0.f, mx = 0.f, my = 0.f, mz = 0.f;
+#pragma unroll
+        for (int a = 1; a < Q; ++a) {
+            float d = 0.f;
+#pragma unroll
+            for (int i = 1; i < Q; ++i)
+                if ((mrt_even_ghost(i) || mrt_odd_ghost(i)) && mrt_coef(i, a) != 0) d += (float)mrt_coef(i, a) * dm[i];
+            fs[a] = f[a] + d;
+            mass += d;
+            mx += ex_of(a) * d;
+            my += ey_of(a) * d;
+            mz += ez_of(a) * d;
+        }
+        // exact momentum F and mass 0 of the update
+        const float cx = 0.5f * (p.Fx - mx), cy = 0.5f * (p.Fy - my), cz = 0.5f * (p.Fz - mz);
+        fs[1] += cx;
+        fs[2] -= cx;
+        fs[3] += cy;
+        fs[4] -= cy;
+        fs[5] += cz;
+        fs[6] -= cz;
+        fs[0] = f[0] - mass;
+        return c;
+    }
     const float uF = ux * p.Fx + uy * p.Fy + uz * p.Fz;
     const float S0 = m.drho - 1.5f * rho * usq;   // isotropic part of (f^eq - w) / w
     const float r45 = 4.5f * rho, r3 = 3.f * rho;
@@ -180,7 +227,7 @@ __device__ __forceinline__ void block_reduce_store(double (&v)[N], double *__res
 // One time step, two lattices: gather from src (streaming + wall reflection),
 // collide, wall treatment, store into the own cell of dst. With STATS the
 // block also writes its FP64 partial plane sums (K_PART values) to part.
-template <typename T, bool STATS>
+template <typename T, bool STATS, int COLL = COLL_BGK>
 __global__ void __launch_bounds__(128) k_step(const T *__restrict__ src, T *__restrict__ dst, Geom g, Phys p,
                                               float *__restrict__ tw_out, double *__restrict__ part)
 {
@@ -192,7 +239,7 @@ __global__ void __launch_bounds__(128) k_step(const T *__restrict__ src, T *__re
 
     float f[Q], fs[Q];
     gather<T>(src, g, p.wall, xc, y, z, f);
-    const CellState c = collide(f, fs, p);
+    const CellState c = collide<COLL>(f, fs, p, row_smag(p, y, g.ny));
 
     float twx = 0.f, twz = 0.f;
     const bool wall_row = (y == 0) || (y == g.ny - 1);

@@ -102,7 +102,8 @@ struct PairState {
 // Only the half sums and differences s/2, d/2 are kept through the collision
 // (the new populations are their sum and difference), which keeps 18 fewer
 // values live.
-__device__ __forceinline__ PairState collide_pair(float2 (&f)[Q], const Phys &p)
+template <int COLL = COLL_BGK>
+__device__ __forceinline__ PairState collide_pair(float2 (&f)[Q], const Phys &p, float smag)
 {
     PairState c;
     // half sums and half differences of the pairs: f_a = hs + hd, f_b = hs - hd
@@ -158,9 +159,104 @@ __device__ __forceinline__ PairState collide_pair(float2 (&f)[Q], const Phys &p)
     float2 omega;
     {
         const float t02 = p.t02;
-        const float cqx = p.smag * sqrtf(q2.x) * (1.f + idev.x), cqy = p.smag * sqrtf(q2.y) * (1.f + idev.y);
+        const float cqx = smag * sqrtf(q2.x) * (1.f + idev.x), cqy = smag * sqrtf(q2.y) * (1.f + idev.y);
         omega = make_float2(2.f / (p.tau0 + sqrtf(t02 + cqx)), 2.f / (p.tau0 + sqrtf(t02 + cqy)));
     }
+    if constexpr (COLL == COLL_MRT) {
+        // MRT (d'Humieres et al. 2002) on the pair sums s = 2 hs and differences
+        // d = 2 hd: non-equilibrium n = s - s^eq, d - d^eq, f0 - f0^eq with
+        //   s^eq = 2 w (S0 + 9/2 rho (e.u)^2), d^eq = 6 w rho (e.u), f0^eq = S0 / 3,
+        // ghost/stress moments m_i = sum coef(i, a) n_a, then
+        //   dm_i = [-s_i m_i + (1 - s_i/2)(gc_i + gu_i . u)] / |row i|^2
+        // and back to the pairs with the same coefficients (orthogonal basis).
+        const float2 usq = fma2(ux, ux, fma2(uy, uy, mul2(uz, uz)));
+        const float2 S0 = fma2(bc(-1.5f), mul2(rho, usq), drho);
+        const float2 r45 = mul2(bc(4.5f), rho), r6 = mul2(bc(6.f), rho);
+        const float2 eus[9] = {ux, uy, uz, add2(ux, uy), add2(ux, uz), add2(uy, uz),
+                               sub2(ux, uy), sub2(ux, uz), sub2(uy, uz)};
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const float w2 = k < 3 ? 2.f / 18.f : 2.f / 36.f;   // 2 w
+            const float2 seq = mul2(bc(w2), fma2(mul2(r45, eus[k]), eus[k], S0));
+            const float2 deq = mul2(bc(0.5f * w2), mul2(r6, eus[k]));
+            hs[k] = sub2(add2(hs[k], hs[k]), seq);   // now the non-equilibrium pair sum
+            hd[k] = sub2(add2(hd[k], hd[k]), deq);   // and difference
+        }
+        const float2 n0 = fma2(bc(-1.f / 3.f), S0, f[0]);
+        float2 dm[Q];
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            if (!mrt_even_ghost(i) && !mrt_odd_ghost(i)) continue;
+            float2 m = bc(0.f);
+            bool first = true;
+            if (mrt_even_ghost(i) && mrt_coef(i, 0) != 0) {
+                m = mul2(bc((float)mrt_coef(i, 0)), n0);
+                first = false;
+            }
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                const int c = mrt_coef(i, 2 * k + 1);
+                if (c == 0) continue;
+                const float2 x = mrt_even_ghost(i) ? hs[k] : hd[k];
+                if (first) {
+                    m = c == 1 ? x : (c == -1 ? mul2(bc(-1.f), x) : mul2(bc((float)c), x));
+                    first = false;
+                } else {
+                    m = c == 1 ? add2(m, x) : (c == -1 ? sub2(m, x) : fma2(bc((float)c), x, m));
+                }
+            }
+            float2 g = bc(p.mrt_gc[i]);
+            if (mrt_even_ghost(i))
+                g = fma2(bc(p.mrt_gu[i][0]), ux, fma2(bc(p.mrt_gu[i][1]), uy, fma2(bc(p.mrt_gu[i][2]), uz, g)));
+            const float inv = 1.f / (float)mrt_norm(i);
+            if (mrt_stress(i)) {
+                const float2 gs = fma2(bc(-0.5f), omega, bc(1.f));   // 1 - s/2
+                dm[i] = mul2(bc(inv), fma2(gs, g, mul2(mul2(bc(-1.f), omega), m)));
+            } else {
+                const float sr = p.mrt_s[i];
+                dm[i] = mul2(bc(inv), fma2(bc(1.f - 0.5f * sr), g, mul2(bc(-sr), m)));
+            }
+        }
+        // back to the pairs: s' = n_s + s^eq + ds, d' = n_d + d^eq + dd
+        float2 mass, mx, my, mz;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const int a = 2 * k + 1;
+            float2 ds = bc(0.f), dd = bc(0.f);
+#pragma unroll
+            for (int i = 1; i < Q; ++i) {
+                const int c = mrt_coef(i, a);
+                if (c == 0) continue;
+                if (mrt_even_ghost(i)) ds = fma2(bc(2.f * c), dm[i], ds);
+                if (mrt_odd_ghost(i)) dd = fma2(bc(2.f * c), dm[i], dd);
+            }
+            const float w2 = k < 3 ? 2.f / 18.f : 2.f / 36.f;
+            const float2 seq = mul2(bc(w2), fma2(mul2(r45, eus[k]), eus[k], S0));
+            const float2 deq = mul2(bc(0.5f * w2), mul2(r6, eus[k]));
+            // ds, dd are the changes of the pair sum and difference
+            mass = k == 0 ? ds : add2(mass, ds);
+            const float2 hdd = mul2(bc(0.5f), dd);
+            if (k == 0) mx = hdd;
+            else if (ex_of(a)) mx = ex_of(a) > 0 ? add2(mx, hdd) : sub2(mx, hdd);
+            if (k == 1) my = hdd;
+            else if (k > 1 && ey_of(a)) my = ey_of(a) > 0 ? add2(my, hdd) : sub2(my, hdd);
+            if (k == 2) mz = hdd;
+            else if (k > 2 && ez_of(a)) mz = ez_of(a) > 0 ? add2(mz, hdd) : sub2(mz, hdd);
+            hs[k] = mul2(bc(0.5f), add2(add2(hs[k], seq), ds));
+            hd[k] = mul2(bc(0.5f), add2(add2(hd[k], deq), dd));
+        }
+        // exact momentum F (the j rows) and mass (rest population) of the update
+        hd[0] = add2(hd[0], sub2(bc(p.hF[0]), mx));
+        hd[1] = add2(hd[1], sub2(bc(p.hF[1]), my));
+        hd[2] = add2(hd[2], sub2(bc(p.hF[2]), mz));
+        f[0] = sub2(f[0], mass);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            f[2 * k + 1] = add2(hs[k], hd[k]);
+            f[2 * k + 2] = sub2(hs[k], hd[k]);
+        }
+        return c;
+    } else {
     const float2 gk = fma2(bc(-0.5f), omega, bc(1.f));
     const float2 nw = mul2(bc(-1.f), omega);                               // -omega
     const float2 usq = fma2(ux, ux, fma2(uy, uy, mul2(uz, uz)));
@@ -213,12 +309,13 @@ __device__ __forceinline__ PairState collide_pair(float2 (&f)[Q], const Phys &p)
         f[2 * k + 2] = sub2(hs[k], hd[k]);
     }
     return c;
+    }
 }
 
 // One tile: the x-pairs xb * blockDim.x + threadIdx.x of row (y, z), i.e.
 // cells [2 xb blockDim.x, 2 (xb + 1) blockDim.x). With STATS the block writes
 // its FP64 partial sums to part_blk[0..K_PART).
-template <typename T, bool STATS>
+template <typename T, bool STATS, int COLL = COLL_BGK>
 __device__ __forceinline__ void pair_tile(const T *__restrict__ src, T *__restrict__ dst, const Geom &g, const Phys &p,
                                           float *__restrict__ tw_out, double *__restrict__ part_blk, int xb, int y,
                                           int z)
@@ -237,7 +334,7 @@ __device__ __forceinline__ void pair_tile(const T *__restrict__ src, T *__restri
     else
         gather_pair<T, ROW_INTERIOR>(src, g, p.wall, xl, y, z, zm, zp, lane, f);
 
-    const PairState c = collide_pair(f, p);
+    const PairState c = collide_pair<COLL>(f, p, row_smag(p, y, g.ny));
 
     float2 twx = bc(0.f), twz = bc(0.f);
     if (y == 0 || y == g.ny - 1) {
@@ -309,14 +406,14 @@ __device__ __forceinline__ void pdl_begin()
 #define LBM_PAIR_MIN_BLOCKS 6   // resident CTAs per SM the register budget must allow (80 registers)
 #endif
 
-template <typename T, bool STATS>
+template <typename T, bool STATS, int COLL = COLL_BGK>
 __global__ void __launch_bounds__(128, LBM_PAIR_MIN_BLOCKS) k_step_pair(const T *__restrict__ src, T *__restrict__ dst, Geom g, Phys p,
                                                    float *__restrict__ tw_out, double *__restrict__ part)
 {
     pdl_begin();
     const int y = blockIdx.y, z = blockIdx.z;
     const long long blk = ((long long)y * g.nz + z) * gridDim.x + blockIdx.x;
-    pair_tile<T, STATS>(src, dst, g, p, tw_out, STATS ? part + blk * K_PART : nullptr, blockIdx.x, y, z);
+    pair_tile<T, STATS, COLL>(src, dst, g, p, tw_out, STATS ? part + blk * K_PART : nullptr, blockIdx.x, y, z);
 }
 
 }  // namespace lbm

@@ -85,14 +85,14 @@ __device__ __forceinline__ void gather_quad(const __half *__restrict__ src, cons
 }
 
 // Collision (and wall layer) of one packed pair held in word H of the quad.
-template <int H, bool STATS>
-__device__ __forceinline__ void quad_half(uint2 (&r)[Q], const Phys &p, bool wall_row, bool bottom, float4 &tw,
-                                          double (&v)[K_PART], bool valid)
+template <int H, bool STATS, int COLL>
+__device__ __forceinline__ void quad_half(uint2 (&r)[Q], const Phys &p, float smag, bool wall_row, bool bottom,
+                                          float4 &tw, double (&v)[K_PART], bool valid)
 {
     float2 f[Q];
 #pragma unroll
     for (int a = 0; a < Q; ++a) f[a] = h2f(H ? r[a].y : r[a].x);
-    const PairState c = collide_pair(f, p);
+    const PairState c = collide_pair<COLL>(f, p, smag);
     float2 twx = bc(0.f), twz = bc(0.f);
     if (wall_row) {
         float fa[Q], fb[Q];
@@ -147,7 +147,7 @@ __device__ __forceinline__ void quad_half(uint2 (&r)[Q], const Phys &p, bool wal
 // One tile: the x-quads xb * blockDim.x + threadIdx.x of row (y, z), i.e.
 // cells [4 xb blockDim.x, 4 (xb + 1) blockDim.x). With STATS the block writes
 // its FP64 partial sums to part_blk[0..K_PART).
-template <bool STATS>
+template <bool STATS, int COLL = COLL_BGK>
 __device__ __forceinline__ void quad_tile(const __half *__restrict__ src, __half *__restrict__ dst, const Geom &g,
                                           const Phys &p, float *__restrict__ tw_out, double *__restrict__ part_blk,
                                           int xb, int y, int z)
@@ -173,8 +173,9 @@ __device__ __forceinline__ void quad_tile(const __half *__restrict__ src, __half
         for (int k = 0; k < K_PART; ++k) v[k] = 0.0;
     }
     float4 twa = make_float4(0.f, 0.f, 0.f, 0.f), twb = twa;
-    quad_half<0, STATS>(r, p, wall_row, y == 0, twa, v, valid);
-    quad_half<1, STATS>(r, p, wall_row, y == 0, twb, v, valid);
+    const float smag = row_smag(p, y, g.ny);
+    quad_half<0, STATS, COLL>(r, p, smag, wall_row, y == 0, twa, v, valid);
+    quad_half<1, STATS, COLL>(r, p, smag, wall_row, y == 0, twb, v, valid);
     if (valid) {
         if (wall_row) {
             float4 *t = reinterpret_cast<float4 *>(reinterpret_cast<float2 *>(tw_out) +
@@ -189,7 +190,7 @@ __device__ __forceinline__ void quad_tile(const __half *__restrict__ src, __half
     if (STATS) block_reduce_store<K_PART>(v, part_blk);
 }
 
-template <bool STATS>
+template <bool STATS, int COLL = COLL_BGK>
 __global__ void __launch_bounds__(128, LBM_QUAD_MIN_BLOCKS) k_step_quad(const __half *__restrict__ src,
                                                                          __half *__restrict__ dst, Geom g, Phys p,
                                                                          float *__restrict__ tw_out,
@@ -198,7 +199,7 @@ __global__ void __launch_bounds__(128, LBM_QUAD_MIN_BLOCKS) k_step_quad(const __
     pdl_begin();
     const int y = blockIdx.y, z = blockIdx.z;
     const long long blk = ((long long)y * g.nz + z) * gridDim.x + blockIdx.x;
-    quad_tile<STATS>(src, dst, g, p, tw_out, STATS ? part + blk * K_PART : nullptr, blockIdx.x, y, z);
+    quad_tile<STATS, COLL>(src, dst, g, p, tw_out, STATS ? part + blk * K_PART : nullptr, blockIdx.x, y, z);
 }
 
 }  // namespace lbm

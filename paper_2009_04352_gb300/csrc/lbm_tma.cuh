@@ -133,7 +133,7 @@ __device__ __forceinline__ void read_rows(const T *stage, int nx, int wall, int 
     }
 }
 
-template <typename T, bool STATS, int NW>
+template <typename T, bool STATS, int NW, int COLL = COLL_BGK>
 __global__ void __launch_bounds__(NW * 32, 16 / NW) k_step_rows(const T *__restrict__ src, T *__restrict__ dst, Geom g, Phys p,
                                                       float *__restrict__ tw_out, double *__restrict__ part,
                                                       int *__restrict__ err, int S)
@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(NW * 32, 16 / NW) k_step_rows(const T *__restr
         for (int x0 = 2 * (warp * 32 + lane); x0 < g.nx; x0 += 64 * NW) {
             float2 f[Q];
             read_rows<T>(stage, g.nx, p.wall, y, g.ny, x0, f);
-            const PairState c = collide_pair(f, p);
+            const PairState c = collide_pair<COLL>(f, p, row_smag(p, y, g.ny));
             float2 twx = bc(0.f), twz = bc(0.f);
             if (wall_row) {
                 float fa[Q], fb[Q];

@@ -29,6 +29,7 @@ LBM_ERR_STATE = -5
 
 WALL_BB, WALL_WFB, WALL_FREESLIP = 0, 1, 2
 KERNEL_AUTO, KERNEL_CELL, KERNEL_PAIR, KERNEL_TMA, KERNEL_QUAD = 0, 1, 2, 3, 4
+COLLISION_BGK, COLLISION_MRT = 0, 1
 FP32, FP16_SHIFTED = 0, 1
 PULL2 = 0
 
@@ -71,6 +72,7 @@ _SIGNATURES = {
     "lbm_get_step": (C.c_longlong, [_VP]),
     "lbm_set_kernel": (C.c_int, [_VP, C.c_int]),
     "lbm_get_kernel": (C.c_int, [_VP]),
+    "lbm_set_les": (C.c_int, [_VP, C.c_int, C.c_double, C.c_double]),
     "lbm_moments": (C.c_int, [_VP, _VP, _VP, C.c_int]),
     "lbm_wall_stress": (C.c_int, [_VP, _VP, C.c_int]),
     "lbm_plane_stats": (C.c_int, [_VP, _DP, _DP, C.POINTER(C.c_longlong), C.c_int]),
@@ -86,6 +88,7 @@ _SIGNATURES = {
     "lbm_batch_get_config": (C.c_int, [_VP, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                        C.POINTER(C.c_longlong)]),
     "lbm_batch_autotune": (C.c_int, [_VP, C.c_int, _DP]),
+    "lbm_batch_set_les": (C.c_int, [_VP, C.c_int, _DP, C.c_double]),
     "lbm_batch_sync": (C.c_int, [_VP]),
     "lbm_batch_destroy": (None, [_VP]),
     "lbm_destroy": (None, [_VP]),
@@ -180,6 +183,10 @@ def lbm_set_kernel(h, kernel):
 
 def lbm_get_kernel(h):
     return int(lib().lbm_get_kernel(h))
+
+
+def lbm_set_les(h, collision, u_tau_ref=0.0, a_plus=0.0):
+    _check(lib().lbm_set_les(h, int(collision), float(u_tau_ref), float(a_plus)))
 
 
 def lbm_moments(h, rho_ptr, u_ptr, on_device):
@@ -277,6 +284,9 @@ class Channel:
     def set_kernel(self, kernel):
         lbm_set_kernel(self._h, kernel)
 
+    def set_les(self, collision=COLLISION_BGK, u_tau_ref=0.0, a_plus=0.0):
+        lbm_set_les(self._h, collision, u_tau_ref, a_plus)
+
     def moments(self, device=False):
         """(rho [nz,ny,nx], u [3,nz,ny,nx]) as FP32 numpy arrays, or torch CUDA
         tensors when device=True."""
@@ -370,6 +380,11 @@ class Batch:
         t, c, g, tl = C.c_int(), C.c_int(), C.c_int(), C.c_longlong()
         _check(lib().lbm_batch_get_config(self._b, C.byref(t), C.byref(c), C.byref(g), C.byref(tl)))
         return {"threads": t.value, "ctas_per_sm": c.value, "grid": g.value, "tiles": tl.value}
+
+    def set_les(self, collision=COLLISION_BGK, u_tau_ref=None, a_plus=0.0):
+        ut = None if u_tau_ref is None else np.ascontiguousarray(np.asarray(u_tau_ref, dtype=np.float64))
+        _check(lib().lbm_batch_set_les(self._b, int(collision), _dp(ut) if ut is not None else None,
+                                       float(a_plus)))
 
     def autotune(self, steps=5):
         ms = C.c_double()
