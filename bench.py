@@ -140,13 +140,17 @@ def dist_env():
     return rank, world, local
 
 
-def time_channel(case, precision, steps, warmup, stream, clocks=None):
-    """Device time of `steps` steps (CUDA events on the handle's stream)."""
+def time_channel(case, precision, steps, warmup, stream, clocks=None, mrt=False):
+    """Device time of `steps` steps (CUDA events on the handle's stream). With
+    mrt the paper's LES operator runs: MRT collision, Smagorinsky with van
+    Driest damping (A+ = 26, reference u_tau of the case)."""
     import torch
     from paper_2009_04352_gb300 import lbm
 
     with torch.cuda.stream(stream):
         ch = lbm.Channel.from_case(case, precision=precision, stream=stream.cuda_stream)
+        if mrt:
+            ch.set_les(lbm.COLLISION_MRT, case.u_tau, 26.0)
         ch.init_channel(workload.u_mean_profile(case), workload.noise_amplitude(case), case.seed)
         ch.step(warmup)
         ch.sync()
@@ -378,10 +382,14 @@ def main():
         for name, prec in (("c5_batch64_fp32", lbm.FP32), ("c5_batch64_fp16", lbm.FP16_SHIFTED)):
             variants[name] = time_batch(prec, 30, stream, peak)
     if not args.no_variants and rank == 0:
-        for name, wl, prec, steps in (("c3_fp32", "c3", lbm.FP32, 2000), ("c3_fp16", "c3", lbm.FP16_SHIFTED, 2000),
-                                      ("c4_fp32", "c4", lbm.FP32, 300), ("c4_fp16", "c4", lbm.FP16_SHIFTED, 300)):
+        for name, wl, prec, steps, mrt in (("c3_fp32", "c3", lbm.FP32, 2000, False),
+                                           ("c3_fp16", "c3", lbm.FP16_SHIFTED, 2000, False),
+                                           ("c4_fp32", "c4", lbm.FP32, 300, False),
+                                           ("c4_fp16", "c4", lbm.FP16_SHIFTED, 300, False),
+                                           ("c3_mrt_vandriest_fp32", "c3", lbm.FP32, 1000, True),
+                                           ("c3_mrt_vandriest_fp16", "c3", lbm.FP16_SHIFTED, 1000, True)):
             c = workload.CASES[wl]
-            vms, vfin = time_channel(c, prec, steps, 20, stream)
+            vms, vfin = time_channel(c, prec, steps, 20, stream, mrt=mrt)
             kms = vms / steps
             gbs = BYTES_PER_LUP[prec] * c.cells / (kms * 1e-3) / 1e9
             variants[name] = {"workload": c.name, "cells": c.cells, "MLUPS": c.cells * steps / (vms * 1e-3) / 1e6,
