@@ -68,6 +68,13 @@ def _load():
                                              C.c_double, dp, dp]),
             "or_wfb_stress": (None, [C.c_double, dp, C.c_double, C.c_double, C.c_double,
                                      C.c_double, dp]),
+            "or_wfb_stress_law": (None, [C.c_int, C.c_double, dp, C.c_double, C.c_double,
+                                         C.c_double, C.c_double, dp]),
+            "or_loglaw_crossing": (C.c_double, [C.c_double, C.c_double]),
+            "or_loglaw_uplus": (C.c_double, [C.c_double, C.c_double, C.c_double]),
+            "or_powerlaw_uplus": (C.c_double, [C.c_double]),
+            "or_wall_uplus": (C.c_double, [C.c_int, C.c_double, C.c_double, C.c_double]),
+            "or_set_wall_law": (C.c_int, [vp, C.c_int]),
             "or_splitmix64": (C.c_uint64, [C.c_uint64]),
             "or_uniform": (C.c_double, [C.c_uint64, C.c_uint64]),
             "or_create": (vp, [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, dp, C.c_int,
@@ -221,6 +228,32 @@ def wfb_stress(rho, u, kappa=0.41, B=5.5, y1=1.0, nu=1e-4):
     return tw
 
 
+LAW_SPALDING, LAW_LOG, LAW_POWER = 0, 1, 2
+
+
+def wfb_stress_law(law, rho, u, kappa=0.41, B=5.5, y1=1.0, nu=1e-4):
+    tw = np.zeros(2)
+    _load().or_wfb_stress_law(int(law), float(rho), _dp(_vec(u, 3)), float(kappa), float(B),
+                              float(y1), float(nu), _dp(tw))
+    return tw
+
+
+def loglaw_crossing(kappa=0.41, B=5.5):
+    return _load().or_loglaw_crossing(float(kappa), float(B))
+
+
+def loglaw_uplus(R, kappa=0.41, B=5.5):
+    return _load().or_loglaw_uplus(float(R), float(kappa), float(B))
+
+
+def powerlaw_uplus(R):
+    return _load().or_powerlaw_uplus(float(R))
+
+
+def wall_uplus(law, R, kappa=0.41, B=5.5):
+    return _load().or_wall_uplus(int(law), float(R), float(kappa), float(B))
+
+
 def splitmix64(s: int) -> int:
     return int(_load().or_splitmix64(C.c_uint64(s & 0xFFFFFFFFFFFFFFFF)))
 
@@ -310,6 +343,11 @@ class Lattice:
 
     def step(self, n=1):
         self._lib.or_step(self._h, int(n))
+
+    def set_wall_law(self, law):
+        """Wall function of the WFB layer: 0 Spalding, 1 log law, 2 power law."""
+        if self._lib.or_set_wall_law(self._h, int(law)) != 0:
+            raise ValueError(f"oracle: unknown wall law {law}")
 
     def set_les(self, collision=0, u_tau=0.0, a_plus=0.0):
         """collision 0 BGK / 1 MRT; van Driest damping when a_plus > 0."""

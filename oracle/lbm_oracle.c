@@ -308,12 +308,17 @@ static double spalding_dyplus(double up, double kappa, double B)
  * laminar one, u_tau = sqrt(nu |u_t| / y1), i.e. u+ = sqrt(R). Iterates until
  * the step is below tol * u+ or max_iter steps. Far in the log layer the
  * laminar guess is large and the first steps shrink u+ by about 1/kappa each,
- * so the cap must be generous (the wall stress uses 1000). Returns the number of steps
- * taken; iterates[0..n] (optional) receives the sequence of u+. */
+ * so the cap must be generous (the wall stress uses 1000). Where the laminar
+ * guess would overflow exp(kappa u+) (kappa sqrt(R) > 700, R above about 3e6)
+ * the first guess is the log law at y+ = R instead, ln(R) / kappa + B, which
+ * lies above the root (y+ = R / u+ < R) so Newton on the convex h still
+ * descends monotonically. Returns the number of steps taken; iterates[0..n]
+ * (optional) receives the sequence of u+. */
 int or_spalding_newton(double R, double kappa, double B, int max_iter, double tol,
                        double *up_out, double *iterates)
 {
     double up = sqrt(R);
+    if (kappa * up > 700.0) up = log(R) / kappa + B;
     int n = 0;
     if (iterates) iterates[0] = up;
     while (n < max_iter) {
@@ -330,22 +335,73 @@ int or_spalding_newton(double R, double kappa, double B, int max_iter, double to
     return n;
 }
 
+/* Other wall functions of the WFB frame (Sec. 2.3: any law that gives tau_w):
+ *  law 1, two-layer log law: u+ = y+ below the crossing y_c of the two
+ *    branches, u+ = ln(y+)/kappa + B above it;
+ *  law 2, power law of Werner & Wengle: u+ = y+ below y+ = A^(1/(1-b)),
+ *    u+ = A (y+)^b above it, A = 8.3, b = 1/7 (point-wise form).
+ * Each returns u+ for R = y1 |u_t| / nu (y+ = R / u+). */
+double or_loglaw_crossing(double kappa, double B)
+{
+    double y = 11.0;   /* y = ln(y)/kappa + B, by Newton from above the root */
+    for (int i = 0; i < 100; ++i) y -= (y - log(y) / kappa - B) / (1.0 - 1.0 / (kappa * y));
+    return y;
+}
+
+double or_loglaw_uplus(double R, double kappa, double B)
+{
+    const double yc = or_loglaw_crossing(kappa, B);
+    if (sqrt(R) <= yc) return sqrt(R);   /* viscous branch: u+ = y+ = R/u+ */
+    double up = yc;                       /* log branch: u+ = ln(R/u+)/kappa + B */
+    for (int i = 0; i < 200; ++i) {
+        const double h = up - log(R / up) / kappa - B;
+        const double step = h / (1.0 + 1.0 / (kappa * up));
+        up -= step;
+        if (fabs(step) <= 1e-15 * up) break;
+    }
+    return up;
+}
+
+double or_powerlaw_uplus(double R)
+{
+    const double A = 8.3, b = 1.0 / 7.0;
+    const double ym = pow(A, 1.0 / (1.0 - b));   /* where the two branches meet */
+    if (sqrt(R) <= ym) return sqrt(R);
+    /* u+ = A (R/u+)^b  ->  u+ = (A R^b)^(1/(1+b)) */
+    return pow(A * pow(R, b), 1.0 / (1.0 + b));
+}
+
+/* u+ of wall function `law` (0 Spalding, 1 log law, 2 power law). */
+double or_wall_uplus(int law, double R, double kappa, double B)
+{
+    if (law == 1) return or_loglaw_uplus(R, kappa, B);
+    if (law == 2) return or_powerlaw_uplus(R);
+    double up;
+    or_spalding_newton(R, kappa, B, 1000, 1e-14, &up, NULL);
+    return up;
+}
+
 /* Wall shear stress vector from the first-layer cell (Eqs. 15-17): magnitude
  * tau_w = rho u_tau^2, direction opposite to the tangential velocity. Zero when
  * the tangential velocity vanishes. tw[0] = tau_w,x, tw[1] = tau_w,z. */
-void or_wfb_stress(double rho, const double *u, double kappa, double B, double y1,
-                   double nu, double *tw)
+void or_wfb_stress_law(int law, double rho, const double *u, double kappa, double B, double y1,
+                       double nu, double *tw)
 {
     double ut = sqrt(u[0] * u[0] + u[2] * u[2]);
     tw[0] = 0.0;
     tw[1] = 0.0;
     if (ut == 0.0) return;
-    double up;
-    or_spalding_newton(y1 * ut / nu, kappa, B, 1000, 1e-14, &up, NULL);
+    const double up = or_wall_uplus(law, y1 * ut / nu, kappa, B);
     double utau = ut / up;
     double taw = rho * utau * utau;
     tw[0] = -u[0] / ut * taw;
     tw[1] = -u[2] / ut * taw;
+}
+
+void or_wfb_stress(double rho, const double *u, double kappa, double B, double y1,
+                   double nu, double *tw)
+{
+    or_wfb_stress_law(0, rho, u, kappa, B, y1, nu, tw);
 }
 
 /* ------------------------------------------------- seeded initial field -- */
@@ -376,6 +432,7 @@ typedef struct {
     double kappa, B, y1, nu;
     int collision;              /* 0 BGK, 1 MRT */
     double vd_utau, vd_aplus;   /* van Driest reference u_tau and A+ (A+ <= 0: off) */
+    int law;                    /* wall function: 0 Spalding, 1 log law, 2 power law */
     double *f, *g;              /* current and next populations [19][n] */
     double *tw;                 /* wall stress of the last step [2][nz][nx][2] */
     double *dfw;                /* Eq. B-1 per wall of the last step [2] */
@@ -517,6 +574,14 @@ long long or_get_step(const or_lattice *L)
 
 /* Collision operator (0 BGK, 1 MRT) and van Driest damping of the
  * Smagorinsky length (a_plus <= 0 turns it off). */
+/* Wall function of the WFB layer (0 Spalding Eq. 16, 1 log law, 2 power law). */
+int or_set_wall_law(or_lattice *L, int law)
+{
+    if (law < 0 || law > 2) return -1;
+    L->law = law;
+    return 0;
+}
+
 void or_set_les(or_lattice *L, int collision, double u_tau, double a_plus)
 {
     L->collision = collision;
@@ -556,7 +621,7 @@ void or_step(or_lattice *L, int nsteps)
                     int wall_id = (y == 0) ? 0 : ((y == ny - 1) ? 1 : -1);
                     double tw[2] = {0.0, 0.0};
                     if (wall_id >= 0 && L->wall == 1)
-                        or_wfb_stress(rho, u, L->kappa, L->B, L->y1, L->nu, tw);
+                        or_wfb_stress_law(L->law, rho, u, L->kappa, L->B, L->y1, L->nu, tw);
                     if (wall_id >= 0 && L->wall == 0) {
                         /* momentum the bounce-back returns to the fluid */
                         int dir = (wall_id == 0) ? -1 : 1;

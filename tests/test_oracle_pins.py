@@ -166,6 +166,25 @@ def test_spalding_log_limit(oracle_lib):
         assert abs(math.log(yp) / kap + B - up) < 2e-3 * up
 
 
+@pytest.mark.parametrize("yplus", [1e5, 3e6, 1e9, 1e12])
+def test_spalding_newton_far_log_layer(oracle_lib, yplus):
+    """Far out (kappa sqrt(R) > 700) the laminar guess would overflow exp; the
+    solver still returns the root of Eq. 16, checked by the explicit forward law."""
+    # u+ from the forward law by bisection (the root lies within 10 of the log law)
+    lo, hi = 1.0, math.log(yplus) / 0.41 + 15.5
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if oracle_lib.spalding_yplus(mid) < yplus:
+            lo = mid
+        else:
+            hi = mid
+    up_true = 0.5 * (lo + hi)
+    R = up_true * yplus
+    up, n, it = oracle_lib.spalding_newton(R)
+    assert math.isfinite(up) and n < 1000
+    assert up == pytest.approx(up_true, rel=1e-12)
+
+
 @pytest.mark.parametrize("yplus", np.logspace(-3, 4, 29))
 def test_spalding_newton_round_trip(oracle_lib, yplus):
     """u+ -> y+ (Eq. 16) -> R = u+ y+ -> Newton -> u+ recovered to 1e-10."""
@@ -482,3 +501,147 @@ def test_mrt_smagorinsky_with_damping(oracle_lib):
     f = _chapman_enskog_f(oracle_lib, 1.0, np.zeros(3), S, tau_t)
     _, _, _, tau = oracle_lib.collide_mrt(f, tau0, cs_eff / damp, np.zeros(3), damp)
     assert abs(tau - tau_t) < 1e-12
+
+
+# ------------------------------------------- other wall functions (Sec. 2.3) --
+# The WFB frame takes tau_w from any wall function. Besides Spalding's law the
+# introduction names the log law and the two-layer power law of Werner and
+# Wengle. Both invert in closed form through the Lambert W function, which the
+# oracle does not use (it iterates Newton or takes powers): the pins below are
+# scipy's W, the explicit forward laws, and the published crossing points.
+
+def _lambertw(x, k=0):
+    from scipy.special import lambertw
+    w = lambertw(x, k)
+    assert abs(w.imag) < 1e-12
+    return float(w.real)
+
+
+def test_loglaw_crossing_closed_form(oracle_lib):
+    """y+ = ln(y+)/kappa + B at the upper root: y = -W_{-1}(-kappa e^{-kappa B}) / kappa
+    (11.45 at kappa = 0.41, B = 5.5)."""
+    for kappa, B in ((0.41, 5.5), (0.4, 5.2), (0.41, 5.0)):
+        yc = -_lambertw(-kappa * math.exp(-kappa * B), -1) / kappa
+        assert oracle_lib.loglaw_crossing(kappa, B) == pytest.approx(yc, rel=1e-13)
+    assert oracle_lib.loglaw_crossing() == pytest.approx(11.445, abs=1e-3)
+
+
+@pytest.mark.parametrize("R", [1.0, 60.0, 131.0, 132.0, 500.0, 1e4, 3.7e5, 1e8])
+def test_loglaw_uplus_lambert(oracle_lib, R):
+    """Viscous branch u+ = sqrt(R) while sqrt(R) <= y_c; log branch
+    u+ = W0(kappa R e^{kappa B}) / kappa (from kappa u+ e^{kappa u+} = kappa R e^{kappa B})."""
+    kappa, B = 0.41, 5.5
+    yc = oracle_lib.loglaw_crossing(kappa, B)
+    up = oracle_lib.loglaw_uplus(R, kappa, B)
+    if math.sqrt(R) <= yc:
+        assert up == math.sqrt(R)
+    else:
+        assert up == pytest.approx(_lambertw(kappa * R * math.exp(kappa * B)) / kappa, rel=1e-13)
+        # forward law: y+ = R / u+ lies on the log line
+        assert up == pytest.approx(math.log(R / up) / kappa + B, rel=1e-13)
+
+
+def test_loglaw_continuous_at_crossing(oracle_lib):
+    yc = oracle_lib.loglaw_crossing()
+    R = yc * yc
+    lo, hi = oracle_lib.loglaw_uplus(R * (1 - 1e-9)), oracle_lib.loglaw_uplus(R * (1 + 1e-9))
+    assert abs(hi - lo) < 1e-7 * yc
+
+
+@pytest.mark.parametrize("yplus", [0.5, 5.0, 11.0, 12.0, 30.0, 300.0, 3000.0, 1e5])
+def test_powerlaw_round_trip(oracle_lib, yplus):
+    """Werner-Wengle: u+ = y+ up to y+ = 8.3^(7/6) (= 11.81), u+ = 8.3 y+^(1/7)
+    beyond; R = u+ y+ of the forward law must give back u+."""
+    ym = 8.3 ** (7.0 / 6.0)
+    up_true = yplus if yplus <= ym else 8.3 * yplus ** (1.0 / 7.0)
+    assert oracle_lib.powerlaw_uplus(up_true * yplus) == pytest.approx(up_true, rel=1e-13)
+
+
+def test_powerlaw_crossing_published(oracle_lib):
+    """The two Werner-Wengle branches meet at y+ = 11.81."""
+    ym = 8.3 ** (7.0 / 6.0)
+    assert ym == pytest.approx(11.81, abs=5e-3)
+    for f in (1 - 1e-9, 1 + 1e-9):
+        assert oracle_lib.powerlaw_uplus(ym * ym * f) == pytest.approx(ym, rel=1e-8)
+
+
+def test_wall_laws_bracket_spalding(oracle_lib):
+    """All three laws agree deep in the sublayer (u+ = y+), and the log law is the
+    outer asymptote of Spalding's law: their relative gap in u+ shrinks
+    monotonically with y+ (Spalding's y+ exceeds the log law's by terms
+    polynomial in u+, against the exponential)."""
+    up = {law: oracle_lib.wall_uplus(law, 1.0) for law in (0, 1, 2)}
+    assert up[1] == up[2] == 1.0
+    assert up[0] == pytest.approx(1.0, rel=1e-3)
+    gaps = []
+    for yp in (1e2, 1e3, 1e5, 1e7, 1e9):
+        upl = math.log(yp) / 0.41 + 5.5
+        R = upl * yp
+        assert oracle_lib.wall_uplus(1, R) == pytest.approx(upl, rel=1e-13)
+        gaps.append(abs(oracle_lib.wall_uplus(0, R) - upl) / upl)
+    assert all(a > b for a, b in zip(gaps, gaps[1:]))
+    assert gaps[-1] < 1e-6
+
+
+@pytest.mark.parametrize("law", [0, 1, 2])
+def test_wfb_stress_law_direction_and_magnitude(oracle_lib, law):
+    """tau_w opposite to u_t (Eq. 15), |tau_w| = rho (|u_t| / u+)^2 with u+ of the
+    chosen law at y+ = y1 u_tau / nu (Eq. 17)."""
+    rng = np.random.default_rng(11 + law)
+    nu, y1, kappa, B = 1e-4, 1.0, 0.41, 5.5
+    for _ in range(20):
+        rho = 1 + 0.01 * rng.random()
+        u = np.array([0.05 * rng.random() - 0.01, 0.01 * rng.random(), 0.02 * rng.random() - 0.01])
+        tw = oracle_lib.wfb_stress_law(law, rho, u, nu=nu, y1=y1)
+        ut = math.hypot(u[0], u[2])
+        tmag = math.hypot(*tw)
+        assert np.allclose(tw / tmag, -np.array([u[0], u[2]]) / ut, atol=1e-14)
+        utau = math.sqrt(tmag / rho)
+        up, yp = ut / utau, y1 * utau / nu
+        if law == 0:
+            assert oracle_lib.spalding_yplus(up) == pytest.approx(yp, rel=1e-9)
+        elif law == 1:
+            exp_up = yp if yp <= oracle_lib.loglaw_crossing() else math.log(yp) / kappa + B
+            assert up == pytest.approx(exp_up, rel=1e-9)
+        else:
+            exp_up = yp if yp <= 8.3 ** (7.0 / 6.0) else 8.3 * yp ** (1.0 / 7.0)
+            assert up == pytest.approx(exp_up, rel=1e-9)
+    assert np.all(oracle_lib.wfb_stress_law(law, 1.0, [0.0, 0.02, 0.0]) == 0.0)
+    if law == 0:
+        u = np.array([0.031, 0.002, -0.007])
+        assert np.array_equal(oracle_lib.wfb_stress_law(0, 1.01, u), oracle_lib.wfb_stress(1.01, u))
+
+
+@pytest.mark.parametrize("law", [1, 2])
+def test_lattice_wall_law_stress_and_budget(oracle_lib, law):
+    """On the lattice the reported wall stress of each wall cell is the chosen
+    law applied to that cell's pre-step moments, and the momentum budget of
+    Eq. 9 / 12b closes with it."""
+    e, _, _, _ = oracle_lib.table()
+    F = np.array([2.2e-7, 0.0, -1.1e-7])
+    L = _seeded(oracle_lib, 12, 8, 10, 1, force=F, amp=6e-3)
+    L.set_wall_law(law)
+    nu = (0.52 - 0.5) / 3.0
+
+    def mom():
+        f = L.populations().reshape(19, -1)
+        return np.array([math.fsum((e[:, c][:, None] * f).ravel()) for c in range(3)])
+
+    for _ in range(3):
+        rho, u = L.moments()
+        rho = rho.reshape(10, 8, 12)
+        u = u.reshape(3, 10, 8, 12)
+        p0 = mom()
+        L.step(1)
+        tw = L.wall_stress()
+        for w, y in ((0, 0), (1, 7)):
+            for z in (0, 3, 9):
+                for x in (0, 5, 11):
+                    expect = oracle_lib.wfb_stress_law(law, rho[z, y, x], u[:, z, y, x], nu=nu)
+                    assert np.allclose(tw[w, z, x], expect, rtol=1e-13, atol=0)
+        p1 = mom()
+        for c, comp in ((0, 0), (2, 1)):
+            expect = L.n * F[c] + math.fsum(tw[..., comp].ravel())
+            assert abs((p1[c] - p0[c]) - expect) <= 1e-13 + 1e-9 * abs(expect)
+    with pytest.raises(ValueError):
+        L.set_wall_law(3)
