@@ -387,8 +387,13 @@ def main():
                                            ("c4_fp32", "c4", lbm.FP32, 300, False),
                                            ("c4_fp16", "c4", lbm.FP16_SHIFTED, 300, False),
                                            ("c3_mrt_vandriest_fp32", "c3", lbm.FP32, 1000, True),
-                                           ("c3_mrt_vandriest_fp16", "c3", lbm.FP16_SHIFTED, 1000, True)):
+                                           ("c3_mrt_vandriest_fp16", "c3", lbm.FP16_SHIFTED, 1000, True),
+                                           ("c3_loglaw_fp32", "c3:log", lbm.FP32, 1000, False),
+                                           ("c3_powerlaw_fp32", "c3:power", lbm.FP32, 1000, False)):
+            wl, _, law = wl.partition(":")
             c = workload.CASES[wl]
+            if law:
+                c = c.with_(wall_law={"log": lbm.LAW_LOG, "power": lbm.LAW_POWER}[law])
             vms, vfin = time_channel(c, prec, steps, 20, stream, mrt=mrt)
             kms = vms / steps
             gbs = BYTES_PER_LUP[prec] * c.cells / (kms * 1e-3) / 1e9

@@ -60,13 +60,32 @@ typedef enum {
     LBM_WALL_FREESLIP = 2   /* specular reflection (Sec. 2.1, Eq. 4); WFB with tau_w = 0 */
 } lbm_wall_kind;
 
+/* Wall function that gives tau_w to the WFB layer. Sec. 2.3 uses Spalding's
+ * law; the WFB frame takes any law that returns tau_w, and the introduction
+ * names the logarithmic law and the two-layer power law of Werner and Wengle.
+ * Each is solved for u+ from R = y+ u+ = y1 |u_t| / nu (Eq. 17):
+ *   SPALDING  y+ = u+ + e^{-kappa B} (e^{kappa u+} - 1 - kappa u+ - (kappa u+)^2/2
+ *             - (kappa u+)^3/6) (Eq. 16), Newton;
+ *   LOG       u+ = y+ below the crossing y_c of y+ and ln(y+)/kappa + B,
+ *             u+ = ln(y+)/kappa + B above it, Newton on the log branch;
+ *   POWER     u+ = y+ below 8.3^(7/6) (11.81), u+ = 8.3 (y+)^(1/7) above it,
+ *             explicit: u+ = 8.3^(7/8) R^(1/8). */
+typedef enum {
+    LBM_LAW_SPALDING = 0,
+    LBM_LAW_LOG = 1,
+    LBM_LAW_POWER = 2
+} lbm_wall_law;
+
 /* Wall model of the WFB boundary (Sec. 2.3). kappa and B are the constants of
- * Spalding's law (Eq. 16; the paper uses 0.41 and 5.5). y1 is the wall
- * distance entering y+ = y1 u_tau / nu (Eq. 17); 1.0 reproduces the first-layer
- * y+ printed in Table 1. nu is the molecular viscosity used by the wall law;
- * a value <= 0 selects (tau - 1/2) / 3. newton_iters caps the Newton
- * iterations per wall cell and step (<= 0 selects 12); iteration stops earlier
- * once every lane of a warp has a relative step below 1e-7. */
+ * Spalding's law (Eq. 16; the paper uses 0.41 and 5.5) and of the log law. y1
+ * is the wall distance entering y+ = y1 u_tau / nu (Eq. 17); 1.0 reproduces
+ * the first-layer y+ printed in Table 1. nu is the molecular viscosity used by
+ * the wall law; a value <= 0 selects (tau - 1/2) / 3. newton_iters caps the
+ * Newton iterations per wall cell and step (<= 0 selects 12); iteration stops
+ * earlier once every lane of a warp has a relative step below 1e-7. law is an
+ * lbm_wall_law (0, the zero-initialised default, is Spalding's law); another
+ * value, or a log law whose two branches never cross (B <= (1 + ln kappa) /
+ * kappa), makes lbm_create / lbm_batch_create fail with LBM_ERR_ARG. */
 typedef struct {
     int kind;            /* lbm_wall_kind */
     double kappa;
@@ -74,6 +93,7 @@ typedef struct {
     double y1;
     double nu;
     int newton_iters;
+    int law;             /* lbm_wall_law */
 } lbm_wall_model;
 
 typedef enum {

@@ -282,9 +282,11 @@ class Lattice:
 
     @classmethod
     def from_case(cls, case, stats_every=0, wall=None):
-        return cls(case.nx, case.ny, case.nz, case.tau, case.cs, case.force,
-                   case.wall if wall is None else wall, case.kappa, case.b_const, case.y1,
-                   case.nu_wall, stats_every)
+        L = cls(case.nx, case.ny, case.nz, case.tau, case.cs, case.force,
+                case.wall if wall is None else wall, case.kappa, case.b_const, case.y1,
+                case.nu_wall, stats_every)
+        L.set_wall_law(getattr(case, "wall_law", 0))
+        return L
 
     def close(self):
         if self._h:

@@ -344,6 +344,9 @@ int lbm_create_handle(lbm_grid g, double tau, double C_s, const double force[3],
     if (!(C_s >= 0.0)) return fail(LBM_ERR_ARG, "C_s must be >= 0");
     if (!force) return fail(LBM_ERR_ARG, "force is NULL");
     if (wm.kind < LBM_WALL_BB || wm.kind > LBM_WALL_FREESLIP) return fail(LBM_ERR_ARG, "unknown wall kind");
+    if (wm.law < LBM_LAW_SPALDING || wm.law > LBM_LAW_POWER) return fail(LBM_ERR_ARG, "unknown wall law");
+    if (wm.law == LBM_LAW_LOG && !(wm.kappa > 0.0 && wm.B > (1.0 + log(wm.kappa)) / wm.kappa))
+        return fail(LBM_ERR_ARG, "log law: y+ and ln(y+)/kappa + B never cross for these kappa, B");
     if (wm.kind == LBM_WALL_WFB && !(wm.kappa > 0.0 && wm.y1 > 0.0))
         return fail(LBM_ERR_ARG, "WFB needs kappa > 0 and y1 > 0");
     if (precision != LBM_FP32 && precision != LBM_FP16_SHIFTED) return fail(LBM_ERR_ARG, "unknown precision");
@@ -371,6 +374,19 @@ int lbm_create_handle(lbm_grid g, double tau, double C_s, const double force[3],
     h->p.ekb = (float)exp(-wm.kappa * wm.B);
     h->p.y1_over_nu = (float)(wm.y1 / nu);
     h->p.newton_iters = wm.newton_iters > 0 ? wm.newton_iters : 12;
+    h->p.law = wm.law;
+    h->p.ikappa = (float)(1.0 / wm.kappa);
+    h->p.pw_a = (float)pow(8.3, 7.0 / 8.0);
+    if (wm.law == LBM_LAW_LOG) {
+        // upper crossing of y+ and ln(y+)/kappa + B: the map y -> ln(y)/kappa + B
+        // contracts (slope 1/(kappa y) < 1) above 1/kappa, so it descends to the
+        // root from any start above it
+        double y = 1e6;
+        for (int i = 0; i < 400; ++i) y = log(y) / wm.kappa + wm.B;
+        h->p.law_r2 = (float)(y * y);
+    } else if (wm.law == LBM_LAW_POWER) {
+        h->p.law_r2 = (float)pow(8.3, 7.0 / 3.0);   // (8.3^(7/6))^2
+    }
     for (int c = 0; c < 3; ++c) h->p.hF[c] = (float)(0.5 * force[c]);
     for (int k = 0; k < 9; ++k) {
         const int a = 2 * k + 1;

@@ -70,6 +70,10 @@ struct Phys {
     float ekb;           // exp(-kappa B)
     float y1_over_nu;    // y1 / nu of the wall law
     int newton_iters;
+    int law;             // LAW_*: wall function that gives tau_w
+    float ikappa;        // 1 / kappa
+    float law_r2;        // R = (y+)^2 where the viscous branch of the log or power law ends
+    float pw_a;          // power law: 8.3^(7/8), u+ = pw_a R^(1/8)
     // derived on the host once, so kernels do not recompute them per tile
     float hF[3];         // F / 2
     float weF[9];        // w_k (e_k . F) for the opposite pairs k = 0..8 (directions 2k+1, 2k+2)
@@ -83,6 +87,7 @@ struct Phys {
 };
 
 enum { COLL_BGK = 0, COLL_MRT = 1 };
+enum { LAW_SPALDING = 0, LAW_LOG = 1, LAW_POWER = 2 };
 
 // Row i, direction a of the D3Q19 MRT moment basis of d'Humieres et al. (2002)
 // (rho, e, eps, j_x, q_x, j_y, q_y, j_z, q_z, 3p_xx, 3pi_xx, p_ww, pi_ww,
@@ -250,6 +255,43 @@ __device__ __forceinline__ float spalding_uplus(float R, const Phys &p, unsigned
         if (__all_sync(mask, done)) break;
     }
     return up;
+}
+
+// Two-layer log law: u+ = sqrt(R) (u+ = y+) while R <= y_c^2, else the root of
+// u+ + (ln u+ - ln R) / kappa - B = 0. That function is concave and increasing,
+// so Newton from the left of the root climbs to it monotonically; the start,
+// one fixed-point step from the log law at y+ = R, lies left of the root for
+// every R above the crossing. Same warp-wide stop as spalding_uplus.
+__device__ __forceinline__ float loglaw_uplus(float R, const Phys &p, unsigned mask)
+{
+    const bool visc = R <= p.law_r2;
+    const float lr = logf(fmaxf(R, p.law_r2));
+    const float u0 = lr * p.ikappa + p.B;
+    float up = u0 - logf(u0) * p.ikappa;
+    for (int it = 0; it < p.newton_iters; ++it) {
+        const float h = up + (logf(up) - lr) * p.ikappa - p.B;
+        const float step = h / (1.f + p.ikappa / up);
+        up -= step;
+        const bool done = visc || fabsf(step) <= 1e-7f * up;
+        if (__all_sync(mask, done)) break;
+    }
+    return visc ? sqrtf(R) : up;
+}
+
+// Werner-Wengle power law: u+ = sqrt(R) while R <= 8.3^(7/3), else
+// u+ = (8.3 R^(1/7))^(7/8) = 8.3^(7/8) R^(1/8), three square roots.
+__device__ __forceinline__ float powerlaw_uplus(float R, const Phys &p)
+{
+    const float r2 = sqrtf(R);
+    return R <= p.law_r2 ? r2 : p.pw_a * sqrtf(sqrtf(r2));
+}
+
+// u+ of the selected wall function (p.law is uniform over the launch).
+__device__ __forceinline__ float wall_uplus(float R, const Phys &p, unsigned mask)
+{
+    if (p.law == LAW_LOG) return loglaw_uplus(R, p, mask);
+    if (p.law == LAW_POWER) return powerlaw_uplus(R, p);
+    return spalding_uplus(R, p, mask);
 }
 
 }  // namespace lbm

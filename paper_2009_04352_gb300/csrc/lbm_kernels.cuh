@@ -170,7 +170,7 @@ __device__ __forceinline__ void wall_layer(float (&fs)[Q], const CellState &c, c
     if (p.wall == WALL_WFB) {
         const float ut = sqrtf(c.ux * c.ux + c.uz * c.uz);
         const float R = fmaxf(p.y1_over_nu * ut, 1e-30f);
-        const float up = spalding_uplus(R, p, lanes);
+        const float up = wall_uplus(R, p, lanes);
         const float utau = ut / up;
         const float tw = c.rho * utau * utau;
         if (ut > 0.f) {

@@ -30,6 +30,7 @@ LBM_ERR_STATE = -5
 WALL_BB, WALL_WFB, WALL_FREESLIP = 0, 1, 2
 KERNEL_AUTO, KERNEL_CELL, KERNEL_PAIR, KERNEL_TMA, KERNEL_QUAD = 0, 1, 2, 3, 4
 COLLISION_BGK, COLLISION_MRT = 0, 1
+LAW_SPALDING, LAW_LOG, LAW_POWER = 0, 1, 2
 FP32, FP16_SHIFTED = 0, 1
 PULL2 = 0
 
@@ -46,7 +47,7 @@ class lbm_grid(C.Structure):
 
 class lbm_wall_model(C.Structure):
     _fields_ = [("kind", C.c_int), ("kappa", C.c_double), ("B", C.c_double), ("y1", C.c_double),
-                ("nu", C.c_double), ("newton_iters", C.c_int)]
+                ("nu", C.c_double), ("newton_iters", C.c_int), ("law", C.c_int)]
 
 
 class lbm_member(C.Structure):
@@ -140,9 +141,9 @@ def _current_stream():
 # ------------------------------------------------------------ raw entry points
 
 def lbm_create(nx, ny, nz, tau, cs, force, wall=WALL_WFB, kappa=0.41, B=5.5, y1=1.0, nu=-1.0,
-               newton_iters=12, precision=FP32, layout=PULL2, stream=None):
+               newton_iters=12, precision=FP32, layout=PULL2, stream=None, law=LAW_SPALDING):
     g = lbm_grid(int(nx), int(ny), int(nz))
-    wm = lbm_wall_model(int(wall), float(kappa), float(B), float(y1), float(nu), int(newton_iters))
+    wm = lbm_wall_model(int(wall), float(kappa), float(B), float(y1), float(nu), int(newton_iters), int(law))
     fvec = np.ascontiguousarray(np.asarray(force, dtype=np.float64).reshape(3))
     out = C.c_void_p()
     s = _current_stream() if stream is None else C.c_void_p(stream)
@@ -229,18 +230,18 @@ class Channel:
     """One channel lattice on the current CUDA device (wraps an lbm_handle)."""
 
     def __init__(self, nx, ny, nz, tau, cs, force, wall=WALL_WFB, kappa=0.41, B=5.5, y1=1.0, nu=-1.0,
-                 newton_iters=12, precision=FP32, layout=PULL2, stream=None):
+                 newton_iters=12, precision=FP32, layout=PULL2, stream=None, law=LAW_SPALDING):
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         self.n = self.nx * self.ny * self.nz
         self.precision = precision
         self._h = lbm_create(nx, ny, nz, tau, cs, force, wall, kappa, B, y1, nu, newton_iters, precision,
-                             layout, stream)
+                             layout, stream, law)
 
     @classmethod
     def from_case(cls, case, precision=FP32, wall=None, stream=None):
         return cls(case.nx, case.ny, case.nz, case.tau, case.cs, case.force,
                    case.wall if wall is None else wall, case.kappa, case.b_const, case.y1,
-                   case.nu_wall, case.newton_iters, precision, PULL2, stream)
+                   case.nu_wall, case.newton_iters, precision, PULL2, stream, case.wall_law)
 
     @property
     def handle(self):
@@ -328,7 +329,8 @@ def member_of(case):
     m.C_s = case.cs
     for i in range(3):
         m.force[i] = case.force[i]
-    m.wall = lbm_wall_model(case.wall, case.kappa, case.b_const, case.y1, case.nu_wall, case.newton_iters)
+    m.wall = lbm_wall_model(case.wall, case.kappa, case.b_const, case.y1, case.nu_wall, case.newton_iters,
+                            case.wall_law)
     return m
 
 

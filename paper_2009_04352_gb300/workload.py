@@ -71,6 +71,7 @@ class ChannelCase:
     nu_wall: float = -1.0         # wall-function viscosity; < 0 means (tau0 - 1/2)/3
     newton_iters: int = 12
     noise_frac: float = NOISE_FRAC
+    wall_law: int = 0             # 0 Spalding (Eq. 16), 1 log law, 2 Werner-Wengle power law
 
     @property
     def cells(self) -> int:

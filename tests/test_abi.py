@@ -55,15 +55,18 @@ def test_invalid_arguments_rejected_without_device():
            dict(nx=8, ny=8, nz=8, tau=0.6, wall=7),    # unknown wall
            dict(nx=8, ny=8, nz=8, tau=0.6, precision=5),
            dict(nx=8, ny=8, nz=8, tau=0.6, layout=3),
-           dict(nx=1 << 16, ny=1 << 10, nz=1 << 10, tau=0.6)]  # > 2^31 cells
+           dict(nx=1 << 16, ny=1 << 10, nz=1 << 10, tau=0.6),  # > 2^31 cells
+           dict(nx=8, ny=8, nz=8, tau=0.6, law=3),     # unknown wall law
+           dict(nx=8, ny=8, nz=8, tau=0.6, law=lbm.LAW_LOG, B=0.2)]  # log branches never cross
     for kw in bad:
         kw = dict(kw)
-        args = dict(cs=0.1, force=(1e-6, 0, 0), wall=lbm.WALL_WFB, precision=lbm.FP32, layout=lbm.PULL2)
+        args = dict(cs=0.1, force=(1e-6, 0, 0), wall=lbm.WALL_WFB, precision=lbm.FP32, layout=lbm.PULL2,
+                    law=lbm.LAW_SPALDING, B=5.5)
         args.update(kw)
         with pytest.raises(lbm.LbmError) as ei:
             lbm.lbm_create(args.pop("nx"), args.pop("ny"), args.pop("nz"), args.pop("tau"), args.pop("cs"),
-                           args.pop("force"), wall=args["wall"], precision=args["precision"],
-                           layout=args["layout"], stream=0)
+                           args.pop("force"), wall=args["wall"], B=args["B"], precision=args["precision"],
+                           layout=args["layout"], stream=0, law=args["law"])
         assert ei.value.code == lbm.LBM_ERR_ARG
         assert lbm.lib().lbm_last_error().decode()
 
