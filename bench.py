@@ -140,15 +140,16 @@ def dist_env():
     return rank, world, local
 
 
-def time_channel(case, precision, steps, warmup, stream, clocks=None, mrt=False):
+def time_channel(case, precision, steps, warmup, stream, clocks=None, mrt=False, layout=0):
     """Device time of `steps` steps (CUDA events on the handle's stream). With
     mrt the paper's LES operator runs: MRT collision, Smagorinsky with van
-    Driest damping (A+ = 26, reference u_tau of the case)."""
+    Driest damping (A+ = 26, reference u_tau of the case). layout 1 is the
+    single-lattice AA layout."""
     import torch
     from paper_2009_04352_gb300 import lbm
 
     with torch.cuda.stream(stream):
-        ch = lbm.Channel.from_case(case, precision=precision, stream=stream.cuda_stream)
+        ch = lbm.Channel.from_case(case, precision=precision, stream=stream.cuda_stream, layout=layout)
         if mrt:
             ch.set_les(lbm.COLLISION_MRT, case.u_tau, 26.0)
         ch.init_channel(workload.u_mean_profile(case), workload.noise_amplitude(case), case.seed)
@@ -388,13 +389,20 @@ def main():
                                            ("c4_fp16", "c4", lbm.FP16_SHIFTED, 300, False),
                                            ("c3_mrt_vandriest_fp32", "c3", lbm.FP32, 1000, True),
                                            ("c3_mrt_vandriest_fp16", "c3", lbm.FP16_SHIFTED, 1000, True),
-                                           ("c3_loglaw_fp32", "c3:log", lbm.FP32, 1000, False),
-                                           ("c3_powerlaw_fp32", "c3:power", lbm.FP32, 1000, False)):
-            wl, _, law = wl.partition(":")
+                                           ("c3_loglaw_fp32", "c3+log", lbm.FP32, 1000, False),
+                                           ("c3_powerlaw_fp32", "c3+power", lbm.FP32, 1000, False),
+                                           ("c3_aa_fp32", "c3+aa", lbm.FP32, 2000, False),
+                                           ("c3_aa_fp16", "c3+aa", lbm.FP16_SHIFTED, 2000, False),
+                                           ("c4_aa_fp32", "c4+aa", lbm.FP32, 300, False),
+                                           ("c4_aa_fp16", "c4+aa", lbm.FP16_SHIFTED, 300, False)):
+            wl, *opts = wl.split("+")
             c = workload.CASES[wl]
-            if law:
-                c = c.with_(wall_law={"log": lbm.LAW_LOG, "power": lbm.LAW_POWER}[law])
-            vms, vfin = time_channel(c, prec, steps, 20, stream, mrt=mrt)
+            if "log" in opts:
+                c = c.with_(wall_law=lbm.LAW_LOG)
+            if "power" in opts:
+                c = c.with_(wall_law=lbm.LAW_POWER)
+            layout = lbm.AA if "aa" in opts else lbm.PULL2
+            vms, vfin = time_channel(c, prec, steps, 20, stream, mrt=mrt, layout=layout)
             kms = vms / steps
             gbs = BYTES_PER_LUP[prec] * c.cells / (kms * 1e-3) / 1e9
             variants[name] = {"workload": c.name, "cells": c.cells, "MLUPS": c.cells * steps / (vms * 1e-3) / 1e6,

@@ -101,8 +101,19 @@ typedef enum {
     LBM_FP16_SHIFTED = 1   /* populations stored as FP16 deviations f_a - w_a */
 } lbm_precision;
 
+/* Storage layout of the populations (both move 19 reads + 19 writes per cell
+ * and step and give bitwise the same results; the paper fixes neither).
+ *   PULL2  two lattices: each step gathers from the neighbours of one array
+ *          and writes the own cell of the other.
+ *   AA     one lattice updated in place (the AA pattern of Bailey et al.
+ *          2009): steps alternate between reading and rewriting the own
+ *          cell's slots and gathering from the neighbours / pushing to them,
+ *          which halves the population memory. Runs the CELL, PAIR and QUAD
+ *          kernel forms; selecting TMA fails with LBM_ERR_ARG. Not available
+ *          for batches. */
 typedef enum {
-    LBM_PULL2 = 0          /* two lattices, gather from neighbours, write own cell */
+    LBM_PULL2 = 0,
+    LBM_AA = 1
 } lbm_layout;
 
 /* Form of the fused step kernel (all compute the same update).
@@ -135,8 +146,9 @@ typedef struct lbm_handle lbm_handle;
  *   cuda_stream  cudaStream_t to order all work on; NULL selects the legacy
  *              default stream.
  *   out        receives the handle.
- * Allocates 2 * 19 * cells populations plus small wall and statistics buffers
- * on the current device. Errors: LBM_ERR_ARG, LBM_ERR_OOM, LBM_ERR_CUDA. */
+ * Allocates 2 * 19 * cells populations (PULL2) or 19 * cells (AA), plus small
+ * wall and statistics buffers, on the current device. Errors: LBM_ERR_ARG,
+ * LBM_ERR_OOM, LBM_ERR_CUDA. */
 int lbm_create(lbm_grid g, double tau, double C_s, const double force[3],
                lbm_wall_model wm, int precision, int layout, void *cuda_stream,
                lbm_handle **out);

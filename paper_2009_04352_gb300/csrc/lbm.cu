@@ -70,6 +70,8 @@ int select_kernel(lbm_handle *h, int kernel)
     if (kernel == LBM_KERNEL_QUAD && !quad)
         return fail(LBM_ERR_ARG, "four-cell kernel needs FP16 storage and nx a multiple of 4");
     if (kernel == LBM_KERNEL_TMA && !seg) return fail(LBM_ERR_ARG, "pipelined kernel needs nx a multiple of 64");
+    if (kernel == LBM_KERNEL_TMA && h->layout == LBM_AA)
+        return fail(LBM_ERR_ARG, "the AA layout runs the cell, pair or quad kernel");
     if (kernel < LBM_KERNEL_CELL || kernel > LBM_KERNEL_QUAD) return fail(LBM_ERR_ARG, "unknown kernel");
     h->kernel = kernel;
     const int per_row = h->g.nx / cells_per_thread(kernel);
@@ -200,6 +202,46 @@ int configure_rows(lbm_handle *h)
 }
 
 // One step with the kernel form of the handle, collision operator COLL.
+// One in-place AA step of kind LAY (even from phase 0, odd from phase 1).
+template <int COLL, int LAY>
+cudaError_t launch_aa(lbm_handle *h, cudaStream_t s, bool stats)
+{
+    const dim3 grid = step_grid(h), block(h->bx);
+    void *f = h->f[0];
+    if (h->kernel == LBM_KERNEL_QUAD) {
+        __half *fh = (__half *)f;
+        return stats ? launch_pdl(lbm::k_step_quad_aa<true, COLL, LAY>, grid, block, 0, s, fh, h->g, h->p, h->tw, h->part)
+                     : launch_pdl(lbm::k_step_quad_aa<false, COLL, LAY>, grid, block, 0, s, fh, h->g, h->p, h->tw,
+                                  h->part);
+    }
+    if (h->kernel == LBM_KERNEL_PAIR) {
+        if (h->precision == LBM_FP16_SHIFTED) {
+            __half *fh = (__half *)f;
+            return stats ? launch_pdl(lbm::k_step_pair_aa<__half, true, COLL, LAY>, grid, block, 0, s, fh, h->g, h->p,
+                                      h->tw, h->part)
+                         : launch_pdl(lbm::k_step_pair_aa<__half, false, COLL, LAY>, grid, block, 0, s, fh, h->g, h->p,
+                                      h->tw, h->part);
+        }
+        float *ff = (float *)f;
+        return stats ? launch_pdl(lbm::k_step_pair_aa<float, true, COLL, LAY>, grid, block, 0, s, ff, h->g, h->p, h->tw,
+                                  h->part)
+                     : launch_pdl(lbm::k_step_pair_aa<float, false, COLL, LAY>, grid, block, 0, s, ff, h->g, h->p,
+                                  h->tw, h->part);
+    }
+    if (h->precision == LBM_FP16_SHIFTED) {
+        if (stats)
+            lbm::k_step_aa<__half, true, COLL, LAY><<<grid, block, 0, s>>>((__half *)f, h->g, h->p, h->tw, h->part);
+        else
+            lbm::k_step_aa<__half, false, COLL, LAY><<<grid, block, 0, s>>>((__half *)f, h->g, h->p, h->tw, h->part);
+    } else {
+        if (stats)
+            lbm::k_step_aa<float, true, COLL, LAY><<<grid, block, 0, s>>>((float *)f, h->g, h->p, h->tw, h->part);
+        else
+            lbm::k_step_aa<float, false, COLL, LAY><<<grid, block, 0, s>>>((float *)f, h->g, h->p, h->tw, h->part);
+    }
+    return cudaSuccess;
+}
+
 template <int COLL>
 int launch_step_c(lbm_handle *h, cudaStream_t s, int src, bool stats)
 {
@@ -208,7 +250,10 @@ int launch_step_c(lbm_handle *h, cudaStream_t s, int src, bool stats)
     const void *a = h->f[src];
     void *b = h->f[src ^ 1];
     cudaError_t e = cudaSuccess;
-    if (h->kernel == LBM_KERNEL_TMA) {
+    if (h->layout == LBM_AA) {
+        // src is the phase: 0 runs the even step, 1 the odd step
+        e = src == 0 ? launch_aa<COLL, lbm::LAY_AA_EVEN>(h, s, stats) : launch_aa<COLL, lbm::LAY_AA_ODD>(h, s, stats);
+    } else if (h->kernel == LBM_KERNEL_TMA) {
         if (half) {
             if (h->tma_warps == 8)
                 launch_rows_t<__half, 8, COLL>(h, s, src, stats);
@@ -318,10 +363,13 @@ int export_state(lbm_handle *h, float *rho, float *u, double *pops, double *part
 {
     const int bx = 128;
     const dim3 grid = grid_of(h, bx);
+    const int map = lbm_state_map(h);
     if (h->precision == LBM_FP16_SHIFTED)
-        lbm::k_export<__half><<<grid, bx, 0, h->stream>>>((const __half *)h->f[h->cur], h->g, h->p, rho, u, pops, part);
+        lbm::k_export<__half><<<grid, bx, 0, h->stream>>>((const __half *)lbm_state_ptr(h), h->g, h->p, map, rho, u,
+                                                          pops, part);
     else
-        lbm::k_export<float><<<grid, bx, 0, h->stream>>>((const float *)h->f[h->cur], h->g, h->p, rho, u, pops, part);
+        lbm::k_export<float><<<grid, bx, 0, h->stream>>>((const float *)lbm_state_ptr(h), h->g, h->p, map, rho, u,
+                                                         pops, part);
     CK_LAUNCH();
     return LBM_OK;
 }
@@ -350,7 +398,8 @@ int lbm_create_handle(lbm_grid g, double tau, double C_s, const double force[3],
     if (wm.kind == LBM_WALL_WFB && !(wm.kappa > 0.0 && wm.y1 > 0.0))
         return fail(LBM_ERR_ARG, "WFB needs kappa > 0 and y1 > 0");
     if (precision != LBM_FP32 && precision != LBM_FP16_SHIFTED) return fail(LBM_ERR_ARG, "unknown precision");
-    if (layout != LBM_PULL2) return fail(LBM_ERR_ARG, "unknown layout");
+    if (layout != LBM_PULL2 && layout != LBM_AA) return fail(LBM_ERR_ARG, "unknown layout");
+    if (layout == LBM_AA && pop0) return fail(LBM_ERR_ARG, "batch members use the two-lattice layout");
     const int sx = (g.nx + 31) / 32 * 32;
     const long long plane = (long long)sx * g.ny * g.nz;
     if (plane > 2147483647LL) return fail(LBM_ERR_ARG, "grid too large (row-padded cells > 2^31 - 1)");
@@ -435,7 +484,7 @@ int lbm_create_handle(lbm_grid g, double tau, double C_s, const double force[3],
         h->f[0] = pop0;
         h->f[1] = pop1;
     }
-    for (int i = 0; i < 2 && !h->member; ++i) {
+    for (int i = 0; i < (layout == LBM_AA ? 1 : 2) && !h->member; ++i) {
         if (cudaMalloc(&h->f[i], bytes) != cudaSuccess) {
             cudaGetLastError();
             return bail(fail(LBM_ERR_OOM, "cannot allocate %zu bytes of populations", bytes));
@@ -509,12 +558,14 @@ int lbm_init_channel(lbm_handle *h, const double *u_mean_x, double noise_amp, ui
     if (cudaMallocAsync((void **)&um, b, h->stream) != cudaSuccess) return fail(LBM_ERR_OOM, "profile buffer");
     CK(cudaMemcpyAsync(um, u_mean_x, b, cudaMemcpyHostToDevice, h->stream));
     const dim3 grid = grid_of(h, 128);
+    if (h->layout == LBM_AA) h->cur = 0;   // written in the natural phase
+    const int map = lbm_state_map(h);
     if (h->precision == LBM_FP16_SHIFTED)
-        lbm::k_init_channel<__half><<<grid, 128, 0, h->stream>>>((__half *)h->f[h->cur], h->g, h->p.wall, um, noise_amp,
-                                                                  seed);
+        lbm::k_init_channel<__half><<<grid, 128, 0, h->stream>>>((__half *)lbm_state_ptr(h), h->g, h->p.wall, map, um,
+                                                                  noise_amp, seed);
     else
-        lbm::k_init_channel<float><<<grid, 128, 0, h->stream>>>((float *)h->f[h->cur], h->g, h->p.wall, um, noise_amp,
-                                                                 seed);
+        lbm::k_init_channel<float><<<grid, 128, 0, h->stream>>>((float *)lbm_state_ptr(h), h->g, h->p.wall, map, um,
+                                                                 noise_amp, seed);
     CK_LAUNCH();
     CK(cudaFreeAsync(um, h->stream));
     // the host profile must stay valid until the copy has run
@@ -531,10 +582,12 @@ int lbm_set_populations(lbm_handle *h, const double *host_in)
     if (cudaMallocAsync((void **)&d, b, h->stream) != cudaSuccess) return fail(LBM_ERR_OOM, "staging buffer");
     CK(cudaMemcpyAsync(d, host_in, b, cudaMemcpyHostToDevice, h->stream));
     const dim3 grid = grid_of(h, 128);
+    if (h->layout == LBM_AA) h->cur = 0;
+    const int map = lbm_state_map(h);
     if (h->precision == LBM_FP16_SHIFTED)
-        lbm::k_scatter<__half><<<grid, 128, 0, h->stream>>>(d, (__half *)h->f[h->cur], h->g, h->p.wall);
+        lbm::k_scatter<__half><<<grid, 128, 0, h->stream>>>(d, (__half *)lbm_state_ptr(h), h->g, h->p.wall, map);
     else
-        lbm::k_scatter<float><<<grid, 128, 0, h->stream>>>(d, (float *)h->f[h->cur], h->g, h->p.wall);
+        lbm::k_scatter<float><<<grid, 128, 0, h->stream>>>(d, (float *)lbm_state_ptr(h), h->g, h->p.wall, map);
     CK_LAUNCH();
     CK(cudaFreeAsync(d, h->stream));
     CK(cudaStreamSynchronize(h->stream));

@@ -9,6 +9,17 @@
 // previous step are taken from the specular (WFB, free-slip) or opposite
 // (bounce-back) slot, so the WFB correction of Eq. 14a,b is added when the
 // wall-bound population is stored.
+//
+// The single-lattice AA layout keeps one array and alternates two step kinds.
+// Where the state is "natural" (phase 0) f_a(x) sits in slot a of x; the even
+// step reads the own slots, collides and writes f*_a into slot opp(a) of the
+// same cell. The state is then in phase 1: f_a(x) is the post-collision value
+// the pull gather would read, kept in the opposite slot (map MAP_AA1 below).
+// The odd step gathers through that map, collides, and pushes f*_a to the slot
+// and cell whose next gather it feeds (push_offset), which restores phase 0.
+// Each thread reads and then rewrites the same set of slots in both kinds
+// (also at the walls, where the specular push of one cell lands in the slots
+// its own gather read), so the update is in place without races.
 #pragma once
 
 #include <cuda_fp16.h>
@@ -49,6 +60,11 @@ __host__ __device__ constexpr double w_of(int a) { return a == 0 ? 1.0 / 3.0 : (
 
 enum { WALL_BB = 0, WALL_WFB = 1, WALL_FREESLIP = 2 };
 enum { ROW_INTERIOR = 0, ROW_BOTTOM = 1, ROW_TOP = 2 };
+// Step kinds: two-lattice pull, AA even step (phase 0 -> 1), AA odd step (1 -> 0).
+enum { LAY_PULL = 0, LAY_AA_EVEN = 1, LAY_AA_ODD = 2 };
+// Where f_a(x) of the current state is stored: after a pull step, in AA
+// phase 0 (own slot), in AA phase 1 (opposite slot of the pull source).
+enum { MAP_PULL = 0, MAP_AA0 = 1, MAP_AA1 = 2 };
 
 // Statistics layout of one block partial: 11 plane sums then 4 wall sums.
 constexpr int K_STATS = 11;
@@ -147,6 +163,14 @@ template <typename T> __device__ __forceinline__ float ld(const T *p);
 template <> __device__ __forceinline__ float ld<float>(const float *p) { return __ldg(p); }
 template <> __device__ __forceinline__ float ld<__half>(const __half *p) { return __half2float(__ldg(p)); }
 
+// Coherent loads for the in-place AA steps (the read-only path of ld() is for
+// arrays that no thread writes during the launch).
+template <typename T> __device__ __forceinline__ float ldc(const T *p);
+template <> __device__ __forceinline__ float ldc<float>(const float *p) { return *p; }
+template <> __device__ __forceinline__ float ldc<__half>(const __half *p) { return __half2float(*p); }
+
+template <typename T, bool NC> __device__ __forceinline__ float ldx(const T *p) { return NC ? ld<T>(p) : ldc<T>(p); }
+
 template <typename T> __device__ __forceinline__ void st(T *p, float v);
 template <> __device__ __forceinline__ void st<float>(float *p, float v) { *p = v; }
 template <> __device__ __forceinline__ void st<__half>(__half *p, float v) { *p = __float2half_rn(v); }
@@ -157,14 +181,14 @@ template <> __device__ __forceinline__ void st<__half>(__half *p, float v) { *p 
 // previous step: the own cell's opposite slot (bounce-back) or the mirrored
 // slot of the cell displaced by the tangential part of e_a (specular, WFB).
 template <int ROW>
-__device__ __forceinline__ long long src_offset(const Geom &g, int wall, int a, int x, int y, int z,
-                                                int xm, int xp, int zm, int zp)
+__device__ __forceinline__ long long src_position(const Geom &g, int wall, int a, int x, int y, int z, int xm,
+                                                  int xp, int zm, int zp, int &slot)
 {
     const int ex = ex_of(a), ey = ey_of(a), ez = ez_of(a);
     int xs = ex == 1 ? xm : (ex == -1 ? xp : x);
     int zs = ez == 1 ? zm : (ez == -1 ? zp : z);
     int ys = y - ey;
-    int slot = a;
+    slot = a;
     const bool crosses = (ROW == ROW_BOTTOM && ey == 1) || (ROW == ROW_TOP && ey == -1);
     if (crosses) {
         ys = y;
@@ -176,7 +200,55 @@ __device__ __forceinline__ long long src_offset(const Geom &g, int wall, int a, 
             slot = mirror_of(a);
         }
     }
-    return (long long)slot * g.plane + ((long long)zs * g.ny + ys) * g.sx + xs;
+    return ((long long)zs * g.ny + ys) * g.sx + xs;
+}
+
+template <int ROW>
+__device__ __forceinline__ long long src_offset(const Geom &g, int wall, int a, int x, int y, int z,
+                                                int xm, int xp, int zm, int zp)
+{
+    int slot;
+    const long long pos = src_position<ROW>(g, wall, a, x, y, z, xm, xp, zm, zp, slot);
+    return (long long)slot * g.plane + pos;
+}
+
+// Element offset of f_a(x, y, z) of the current state under storage map MAP.
+template <int ROW, int MAP>
+__device__ __forceinline__ long long map_offset(const Geom &g, int wall, int a, int x, int y, int z, int xm, int xp,
+                                                int zm, int zp)
+{
+    if (MAP == MAP_AA0) return (long long)a * g.plane + ((long long)z * g.ny + y) * g.sx + x;
+    int slot;
+    const long long pos = src_position<ROW>(g, wall, a, x, y, z, xm, xp, zm, zp, slot);
+    return (long long)(MAP == MAP_AA1 ? opp_of(slot) : slot) * g.plane + pos;
+}
+
+// AA odd step: where f*_a of cell (x, y, z) goes so that the following even
+// step finds it as f_b of the cell it streams to (the inverse of the pull
+// gather): slot a of x + e_a; a wall-bound population goes to the opposite
+// slot of the own cell (bounce-back) or to the mirrored slot of the cell
+// displaced by its tangential velocity (WFB, free slip).
+template <int ROW>
+__device__ __forceinline__ long long push_offset(const Geom &g, int wall, int a, int x, int y, int z, int xm, int xp,
+                                                 int zm, int zp)
+{
+    const int ex = ex_of(a), ey = ey_of(a), ez = ez_of(a);
+    int xt = ex == 1 ? xp : (ex == -1 ? xm : x);
+    int zt = ez == 1 ? zp : (ez == -1 ? zm : z);
+    int yt = y + ey;
+    int slot = a;
+    const bool crosses = (ROW == ROW_BOTTOM && ey == -1) || (ROW == ROW_TOP && ey == 1);
+    if (crosses) {
+        yt = y;
+        if (wall == WALL_BB) {
+            xt = x;
+            zt = z;
+            slot = opp_of(a);
+        } else {
+            slot = mirror_of(a);
+        }
+    }
+    return (long long)slot * g.plane + ((long long)zt * g.ny + yt) * g.sx + xt;
 }
 
 struct Nbr {
@@ -193,25 +265,55 @@ __device__ __forceinline__ Nbr neighbours(const Geom &g, int x, int z)
     return n;
 }
 
-template <typename T, int ROW>
-__device__ __forceinline__ void gather_row(const T *__restrict__ src, const Geom &g, int wall, int x, int y,
-                                           int z, const Nbr &n, float (&fb)[Q])
+template <typename T, int ROW, int MAP, bool NC>
+__device__ __forceinline__ void gather_row(const T *src, const Geom &g, int wall, int x, int y, int z, const Nbr &n,
+                                           float (&fb)[Q])
 {
 #pragma unroll
-    for (int a = 0; a < Q; ++a) fb[a] = ld<T>(src + src_offset<ROW>(g, wall, a, x, y, z, n.xm, n.xp, n.zm, n.zp));
+    for (int a = 0; a < Q; ++a)
+        fb[a] = ldx<T, NC>(src + map_offset<ROW, MAP>(g, wall, a, x, y, z, n.xm, n.xp, n.zm, n.zp));
 }
 
-template <typename T>
-__device__ __forceinline__ void gather(const T *__restrict__ src, const Geom &g, int wall, int x, int y, int z,
-                                       float (&fb)[Q])
+// f(t) of one cell under storage map MAP (NC: the array is not written
+// during the launch, so the read-only path may serve it).
+template <typename T, int MAP = MAP_PULL, bool NC = true>
+__device__ __forceinline__ void gather(const T *src, const Geom &g, int wall, int x, int y, int z, float (&fb)[Q])
 {
     const Nbr n = neighbours(g, x, z);
     if (y == 0)
-        gather_row<T, ROW_BOTTOM>(src, g, wall, x, y, z, n, fb);
+        gather_row<T, ROW_BOTTOM, MAP, NC>(src, g, wall, x, y, z, n, fb);
     else if (y == g.ny - 1)
-        gather_row<T, ROW_TOP>(src, g, wall, x, y, z, n, fb);
+        gather_row<T, ROW_TOP, MAP, NC>(src, g, wall, x, y, z, n, fb);
     else
-        gather_row<T, ROW_INTERIOR>(src, g, wall, x, y, z, n, fb);
+        gather_row<T, ROW_INTERIOR, MAP, NC>(src, g, wall, x, y, z, n, fb);
+}
+
+// gather() with the map chosen at run time (exports, off the hot path).
+template <typename T>
+__device__ __forceinline__ void gather_any(const T *src, const Geom &g, int wall, int map, int x, int y, int z,
+                                           float (&fb)[Q])
+{
+    if (map == MAP_AA0)
+        gather<T, MAP_AA0>(src, g, wall, x, y, z, fb);
+    else if (map == MAP_AA1)
+        gather<T, MAP_AA1>(src, g, wall, x, y, z, fb);
+    else
+        gather<T, MAP_PULL>(src, g, wall, x, y, z, fb);
+}
+
+// Element offset of f_a(x, y, z) under the run-time map (for writers of the state).
+__device__ __forceinline__ long long state_offset(const Geom &g, int wall, int map, int a, int x, int y, int z,
+                                                  const Nbr &n)
+{
+    if (map == MAP_AA0) return map_offset<ROW_INTERIOR, MAP_AA0>(g, wall, a, x, y, z, n.xm, n.xp, n.zm, n.zp);
+    if (y == 0)
+        return map == MAP_AA1 ? map_offset<ROW_BOTTOM, MAP_AA1>(g, wall, a, x, y, z, n.xm, n.xp, n.zm, n.zp)
+                              : map_offset<ROW_BOTTOM, MAP_PULL>(g, wall, a, x, y, z, n.xm, n.xp, n.zm, n.zp);
+    if (y == g.ny - 1)
+        return map == MAP_AA1 ? map_offset<ROW_TOP, MAP_AA1>(g, wall, a, x, y, z, n.xm, n.xp, n.zm, n.zp)
+                              : map_offset<ROW_TOP, MAP_PULL>(g, wall, a, x, y, z, n.xm, n.xp, n.zm, n.zp);
+    return map == MAP_AA1 ? map_offset<ROW_INTERIOR, MAP_AA1>(g, wall, a, x, y, z, n.xm, n.xp, n.zm, n.zp)
+                          : map_offset<ROW_INTERIOR, MAP_PULL>(g, wall, a, x, y, z, n.xm, n.xp, n.zm, n.zp);
 }
 
 // Moments of the deviations: drho = sum fb (rho - 1) and j = sum e fb

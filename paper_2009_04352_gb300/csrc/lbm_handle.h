@@ -14,8 +14,8 @@ struct lbm_handle {
     int layout;
     cudaStream_t stream;
     cudaStream_t cap;            // private stream used only for graph capture
-    void *f[2];                  // two lattices
-    int cur;                     // lattice holding the current post-collision state
+    void *f[2];                  // two lattices (AA: f[0] only)
+    int cur;                     // PULL2: lattice holding the current state; AA: phase (0 or 1)
     long long step;
     int stats_every;
     float *tw;                   // [2][nz][nx][2]
@@ -35,6 +35,14 @@ struct lbm_handle {
     bool member;                 // member view of a batch: populations owned by the batch
     double nu_wall;              // viscosity of the wall law and of the van Driest y+
 };
+
+// The array holding the current state and the map under which f(t) is stored.
+inline void *lbm_state_ptr(const lbm_handle *h) { return h->layout == LBM_AA ? h->f[0] : h->f[h->cur]; }
+inline int lbm_state_map(const lbm_handle *h)
+{
+    if (h->layout != LBM_AA) return lbm::MAP_PULL;
+    return h->cur ? lbm::MAP_AA1 : lbm::MAP_AA0;
+}
 
 // Set the LES model of a handle's physics: collision (COLL_BGK / COLL_MRT)
 // and the van Driest factor (u_tau > 0 and a_plus > 0, else no damping).

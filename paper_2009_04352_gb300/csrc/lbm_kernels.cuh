@@ -200,6 +200,30 @@ __device__ __forceinline__ void wall_layer(float (&fs)[Q], const CellState &c, c
     }
 }
 
+// Add one cell to the FP64 partial statistics (K_STATS plane sums, then the
+// wall sums tau_x, tau_z, |tau|, |tau|^2). Every rounding is explicit, so the
+// sums do not depend on how the compiler contracts them in a given kernel.
+__device__ __forceinline__ void accumulate_cell(double (&v)[K_PART], double r, double ux, double uy, double uz,
+                                                double tx, double tz)
+{
+    const double m2 = __fma_rn(tz, tz, __dmul_rn(tx, tx));
+    v[0] = __dadd_rn(v[0], r);
+    v[1] = __dadd_rn(v[1], ux);
+    v[2] = __dadd_rn(v[2], uy);
+    v[3] = __dadd_rn(v[3], uz);
+    v[4] = __fma_rn(ux, ux, v[4]);
+    v[5] = __fma_rn(uy, uy, v[5]);
+    v[6] = __fma_rn(uz, uz, v[6]);
+    v[7] = __fma_rn(ux, uy, v[7]);
+    v[8] = __fma_rn(r, ux, v[8]);
+    v[9] = __fma_rn(r, uy, v[9]);
+    v[10] = __fma_rn(r, uz, v[10]);
+    v[11] = __dadd_rn(v[11], tx);
+    v[12] = __dadd_rn(v[12], tz);
+    v[13] = __dadd_rn(v[13], __dsqrt_rn(m2));
+    v[14] = __dadd_rn(v[14], m2);
+}
+
 template <int N>
 __device__ __forceinline__ void block_reduce_store(double (&v)[N], double *__restrict__ out)
 {
@@ -227,9 +251,14 @@ __device__ __forceinline__ void block_reduce_store(double (&v)[N], double *__res
 // One time step, two lattices: gather from src (streaming + wall reflection),
 // collide, wall treatment, store into the own cell of dst. With STATS the
 // block also writes its FP64 partial plane sums (K_PART values) to part.
-template <typename T, bool STATS, int COLL = COLL_BGK>
-__global__ void __launch_bounds__(128) k_step(const T *__restrict__ src, T *__restrict__ dst, Geom g, Phys p,
-                                              float *__restrict__ tw_out, double *__restrict__ part)
+//
+// LAY selects the storage scheme: LAY_PULL reads src through the pull map and
+// writes the own cell of dst; the AA kinds (src == dst, one array) read
+// through the phase map and write the opposite own slot (even) or push to the
+// cell the population streams to (odd).
+template <typename T, bool STATS, int COLL, int LAY>
+__device__ __forceinline__ void cell_step(const T *src, T *dst, const Geom &g, const Phys &p, float *tw_out,
+                                          double *part)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y, z = blockIdx.z;
@@ -238,7 +267,12 @@ __global__ void __launch_bounds__(128) k_step(const T *__restrict__ src, T *__re
     const int xc = valid ? x : 0;
 
     float f[Q], fs[Q];
-    gather<T>(src, g, p.wall, xc, y, z, f);
+    if (LAY == LAY_PULL)
+        gather<T, MAP_PULL, true>(src, g, p.wall, xc, y, z, f);
+    else if (LAY == LAY_AA_EVEN)
+        gather<T, MAP_AA0, false>(src, g, p.wall, xc, y, z, f);
+    else
+        gather<T, MAP_AA1, false>(src, g, p.wall, xc, y, z, f);
     const CellState c = collide<COLL>(f, fs, p, row_smag(p, y, g.ny));
 
     float twx = 0.f, twz = 0.f;
@@ -259,33 +293,50 @@ __global__ void __launch_bounds__(128) k_step(const T *__restrict__ src, T *__re
         }
     }
     if (valid) {
-        T *d = dst + ((long long)z * g.ny + y) * g.sx + x;
+        if (LAY == LAY_AA_ODD) {
+            const Nbr n = neighbours(g, x, z);
+            if (y == 0) {
 #pragma unroll
-        for (int a = 0; a < Q; ++a) st<T>(d + a * g.plane, fs[a]);
+                for (int a = 0; a < Q; ++a)
+                    st<T>(dst + push_offset<ROW_BOTTOM>(g, p.wall, a, x, y, z, n.xm, n.xp, n.zm, n.zp), fs[a]);
+            } else if (y == g.ny - 1) {
+#pragma unroll
+                for (int a = 0; a < Q; ++a)
+                    st<T>(dst + push_offset<ROW_TOP>(g, p.wall, a, x, y, z, n.xm, n.xp, n.zm, n.zp), fs[a]);
+            } else {
+#pragma unroll
+                for (int a = 0; a < Q; ++a)
+                    st<T>(dst + push_offset<ROW_INTERIOR>(g, p.wall, a, x, y, z, n.xm, n.xp, n.zm, n.zp), fs[a]);
+            }
+        } else {
+            T *d = dst + ((long long)z * g.ny + y) * g.sx + x;
+#pragma unroll
+            for (int a = 0; a < Q; ++a) st<T>(d + (LAY == LAY_AA_EVEN ? opp_of(a) : a) * g.plane, fs[a]);
+        }
     }
     if (STATS) {
         double v[K_PART];
-        const double r = c.rho, ux = c.ux, uy = c.uy, uz = c.uz;
-        const double tx = twx, tz = twz, m2 = tx * tx + tz * tz;
-        const double on = valid ? 1.0 : 0.0;
-        v[0] = on * r;
-        v[1] = on * ux;
-        v[2] = on * uy;
-        v[3] = on * uz;
-        v[4] = on * ux * ux;
-        v[5] = on * uy * uy;
-        v[6] = on * uz * uz;
-        v[7] = on * ux * uy;
-        v[8] = on * r * ux;
-        v[9] = on * r * uy;
-        v[10] = on * r * uz;
-        v[11] = on * tx;
-        v[12] = on * tz;
-        v[13] = on * sqrt(m2);
-        v[14] = on * m2;
+#pragma unroll
+        for (int k = 0; k < K_PART; ++k) v[k] = 0.0;
+        if (valid) accumulate_cell(v, c.rho, c.ux, c.uy, c.uz, twx, twz);
         const long long blk = ((long long)y * g.nz + z) * gridDim.x + blockIdx.x;
         block_reduce_store<K_PART>(v, part + blk * K_PART);
     }
+}
+
+template <typename T, bool STATS, int COLL = COLL_BGK>
+__global__ void __launch_bounds__(128) k_step(const T *__restrict__ src, T *__restrict__ dst, Geom g, Phys p,
+                                              float *__restrict__ tw_out, double *__restrict__ part)
+{
+    cell_step<T, STATS, COLL, LAY_PULL>(src, dst, g, p, tw_out, part);
+}
+
+// The one-cell step on the single AA array (LAY_AA_EVEN or LAY_AA_ODD).
+template <typename T, bool STATS, int COLL, int LAY>
+__global__ void __launch_bounds__(128) k_step_aa(T *f, Geom g, Phys p, float *__restrict__ tw_out,
+                                                 double *__restrict__ part)
+{
+    cell_step<T, STATS, COLL, LAY>(f, f, g, p, tw_out, part);
 }
 
 // Sum the block partials of each plane (one block per plane, fixed order, so
@@ -316,16 +367,16 @@ static __global__ void k_reduce_planes(const double *__restrict__ part, long lon
 // moments (FP32), unshifted populations (FP64) and FP64 block partials of
 // (sum f - 1, sum e f) for the conservation check.
 template <typename T>
-__global__ void __launch_bounds__(256) k_export(const T *__restrict__ src, Geom g, Phys p, float *__restrict__ rho_out,
-                                                float *__restrict__ u_out, double *__restrict__ pop_out,
-                                                double *__restrict__ part)
+__global__ void __launch_bounds__(256) k_export(const T *__restrict__ src, Geom g, Phys p, int map,
+                                                float *__restrict__ rho_out, float *__restrict__ u_out,
+                                                double *__restrict__ pop_out, double *__restrict__ part)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y, z = blockIdx.z;
     const bool valid = x < g.nx;
     const int xc = valid ? x : 0;
     float f[Q];
-    gather<T>(src, g, p.wall, xc, y, z, f);
+    gather_any<T>(src, g, p.wall, map, xc, y, z, f);
     const long long n = (long long)g.nx * g.ny * g.nz;
     const long long cell = ((long long)z * g.ny + y) * g.nx + x;
     if (valid) {
@@ -375,9 +426,10 @@ template <> __device__ __forceinline__ void st_d<float>(float *p, double v) { *p
 template <> __device__ __forceinline__ void st_d<__half>(__half *p, double v) { *p = __double2half(v); }
 
 // Write f_a(x) (FP64, unshifted, dense) into the slot that the gather of
-// (x, a) reads, so that the next gather returns exactly these populations.
+// (x, a) reads under storage map `map`, so that the next gather returns
+// exactly these populations.
 template <typename T>
-__global__ void k_scatter(const double *__restrict__ in, T *__restrict__ dst, Geom g, int wall)
+__global__ void k_scatter(const double *__restrict__ in, T *__restrict__ dst, Geom g, int wall, int map)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y, z = blockIdx.z;
@@ -386,16 +438,7 @@ __global__ void k_scatter(const double *__restrict__ in, T *__restrict__ dst, Ge
     const long long ncell = (long long)g.nx * g.ny * g.nz;
     const long long cell = ((long long)z * g.ny + y) * g.nx + x;
 #pragma unroll
-    for (int a = 0; a < Q; ++a) {
-        long long off;
-        if (y == 0)
-            off = src_offset<ROW_BOTTOM>(g, wall, a, x, y, z, n.xm, n.xp, n.zm, n.zp);
-        else if (y == g.ny - 1)
-            off = src_offset<ROW_TOP>(g, wall, a, x, y, z, n.xm, n.xp, n.zm, n.zp);
-        else
-            off = src_offset<ROW_INTERIOR>(g, wall, a, x, y, z, n.xm, n.xp, n.zm, n.zp);
-        st_d<T>(dst + off, in[a * ncell + cell] - w_of(a));
-    }
+    for (int a = 0; a < Q; ++a) st_d<T>(dst + state_offset(g, wall, map, a, x, y, z, n), in[a * ncell + cell] - w_of(a));
 }
 
 // SplitMix64 (Steele, Lea & Flood 2014): first output for state s.
@@ -411,8 +454,8 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t s)
 // FP64 without contraction, then rounded once to the storage precision and
 // written to the slots the next gather reads.
 template <typename T>
-__global__ void k_init_channel(T *__restrict__ dst, Geom g, int wall, const double *__restrict__ umean, double amp,
-                               uint64_t seed)
+__global__ void k_init_channel(T *__restrict__ dst, Geom g, int wall, int map, const double *__restrict__ umean,
+                               double amp, uint64_t seed)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y, z = blockIdx.z;
@@ -435,14 +478,7 @@ __global__ void k_init_channel(T *__restrict__ dst, Geom g, int wall, const doub
         const double poly = __dsub_rn(__dadd_rn(__dadd_rn(1.0, __dmul_rn(3.0, eu)), __dmul_rn(__dmul_rn(4.5, eu), eu)),
                                       __dmul_rn(1.5, uu));
         const double feq = __dmul_rn(__dmul_rn(w_of(a), 1.0), poly);
-        long long off;
-        if (y == 0)
-            off = src_offset<ROW_BOTTOM>(g, wall, a, x, y, z, n.xm, n.xp, n.zm, n.zp);
-        else if (y == g.ny - 1)
-            off = src_offset<ROW_TOP>(g, wall, a, x, y, z, n.xm, n.xp, n.zm, n.zp);
-        else
-            off = src_offset<ROW_INTERIOR>(g, wall, a, x, y, z, n.xm, n.xp, n.zm, n.zp);
-        st_d<T>(dst + off, __dsub_rn(feq, w_of(a)));
+        st_d<T>(dst + state_offset(g, wall, map, a, x, y, z, n), __dsub_rn(feq, w_of(a)));
     }
 }
 

@@ -54,7 +54,7 @@ int scratch_on_current_device(double **out)
 // block (b, y) covers the cells of plane y with z = b, b + 8, ...
 template <typename T>
 __global__ void __launch_bounds__(256) k_profile_partials(const T *__restrict__ src, lbm::Geom g, lbm::Phys p,
-                                                         double *__restrict__ scratch)
+                                                         int map, double *__restrict__ scratch)
 {
     const int y = blockIdx.y;
     double v[lbm::K_STATS];
@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(256) k_profile_partials(const T *__restrict__ 
     for (int z = blockIdx.x; z < g.nz; z += kBlocksPerPlane) {
         for (int x = threadIdx.x; x < g.nx; x += blockDim.x) {
             float f[lbm::Q];
-            lbm::gather<T>(src, g, p.wall, x, y, z, f);
+            lbm::gather_any<T>(src, g, p.wall, map, x, y, z, f);
             const lbm::CellState c = lbm::velocity(lbm::moments_of(f), p);
             const double r = c.rho, ux = c.ux, uy = c.uy, uz = c.uz;
             v[0] += r;
@@ -105,9 +105,11 @@ extern "C" int lbm_plane_profile_noalloc(lbm_handle *h, double *out_dev)
     if (rc != LBM_OK) return rc;
     const dim3 grid(kBlocksPerPlane, h->g.ny);
     if (h->precision == LBM_FP16_SHIFTED)
-        k_profile_partials<__half><<<grid, 256, 0, h->stream>>>((const __half *)h->f[h->cur], h->g, h->p, scratch);
+        k_profile_partials<__half><<<grid, 256, 0, h->stream>>>((const __half *)lbm_state_ptr(h), h->g, h->p,
+                                                                lbm_state_map(h), scratch);
     else
-        k_profile_partials<float><<<grid, 256, 0, h->stream>>>((const float *)h->f[h->cur], h->g, h->p, scratch);
+        k_profile_partials<float><<<grid, 256, 0, h->stream>>>((const float *)lbm_state_ptr(h), h->g, h->p,
+                                                               lbm_state_map(h), scratch);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return lbm_record_error(LBM_ERR_CUDA, cudaGetErrorString(e));
     const int n = h->g.ny * lbm::K_STATS;

@@ -30,6 +30,17 @@ template <> __device__ __forceinline__ float2 ld2<__half>(const __half *p)
     return __half22float2(__ldg(reinterpret_cast<const __half2 *>(p)));
 }
 
+// coherent 2-wide loads for the in-place AA steps
+template <typename T> __device__ __forceinline__ float2 ldc2(const T *p);
+template <> __device__ __forceinline__ float2 ldc2<float>(const float *p)
+{
+    return *reinterpret_cast<const float2 *>(p);
+}
+template <> __device__ __forceinline__ float2 ldc2<__half>(const __half *p)
+{
+    return __half22float2(*reinterpret_cast<const __half2 *>(p));
+}
+
 template <typename T> __device__ __forceinline__ void st2(T *p, float2 v);
 template <> __device__ __forceinline__ void st2<float>(float *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
 template <> __device__ __forceinline__ void st2<__half>(__half *p, float2 v)
@@ -39,51 +50,131 @@ template <> __device__ __forceinline__ void st2<__half>(__half *p, float2 v)
 
 // Values of one source row for the pair (x0, x0 + 1) shifted by SH: the cells
 // read x0 - SH and x0 + 1 - SH. `row` points at the start of the source row.
-template <typename T, int SH>
-__device__ __forceinline__ float2 row_pair(const T *__restrict__ row, int x0, int nx, int lane)
+template <typename T, int SH, bool NC = true>
+__device__ __forceinline__ float2 row_pair(const T *row, int x0, int nx, int lane)
 {
-    const float2 v = ld2<T>(row + x0);
+    const float2 v = NC ? ld2<T>(row + x0) : ldc2<T>(row + x0);
     if (SH == 0) return v;
     if (SH == 1) {
         float l = __shfl_up_sync(0xffffffffu, v.y, 1);
-        if (lane == 0 || x0 == 0) l = ld<T>(row + (x0 == 0 ? nx - 1 : x0 - 1));
+        if (lane == 0 || x0 == 0) l = ldx<T, NC>(row + (x0 == 0 ? nx - 1 : x0 - 1));
         return make_float2(l, v.x);
     }
     float r = __shfl_down_sync(0xffffffffu, v.x, 1);
-    if (lane == 31 || x0 + 2 >= nx) r = ld<T>(row + (x0 + 2 >= nx ? x0 + 2 - nx : x0 + 2));
+    if (lane == 31 || x0 + 2 >= nx) r = ldx<T, NC>(row + (x0 + 2 >= nx ? x0 + 2 - nx : x0 + 2));
     return make_float2(v.y, r);
 }
 
 // Gather of the 19 populations of the pair (streaming with the wall
-// reflection of lbm_device.cuh's src_offset, two cells at a time).
+// reflection of lbm_device.cuh's src_offset, two cells at a time). LAY_PULL
+// reads the pull map through the read-only path; LAY_AA_ODD reads the same
+// positions in the opposite slots (map MAP_AA1); LAY_AA_EVEN reads the own
+// slots (map MAP_AA0).
+template <typename T, int ROW, int LAY = LAY_PULL>
+__device__ __forceinline__ void gather_pair(const T *src, const Geom &g, int wall, int x0, int y, int z, int zm,
+                                            int zp, int lane, float2 (&f)[Q])
+{
+    constexpr bool NC = LAY == LAY_PULL;
+    if constexpr (LAY == LAY_AA_EVEN) {
+        const T *own = src + ((long long)z * g.ny + y) * g.sx + x0;
+#pragma unroll
+        for (int a = 0; a < Q; ++a) f[a] = ldc2<T>(own + a * g.plane);
+    } else {
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            const int ex = ex_of(a), ey = ey_of(a), ez = ez_of(a);
+            const bool crosses = (ROW == ROW_BOTTOM && ey == 1) || (ROW == ROW_TOP && ey == -1);
+            const int zs = ez == 1 ? zm : (ez == -1 ? zp : z);
+            const int sa = LAY == LAY_AA_ODD ? opp_of(a) : a;
+            if (!crosses) {
+                const T *row = src + (long long)sa * g.plane + ((long long)zs * g.ny + (y - ey)) * g.sx;
+                if (ex == 1)
+                    f[a] = row_pair<T, 1, NC>(row, x0, g.nx, lane);
+                else if (ex == -1)
+                    f[a] = row_pair<T, -1, NC>(row, x0, g.nx, lane);
+                else
+                    f[a] = row_pair<T, 0, NC>(row, x0, g.nx, lane);
+            } else if (wall == WALL_BB) {
+                const int sb = LAY == LAY_AA_ODD ? a : opp_of(a);
+                const T *row = src + (long long)sb * g.plane + ((long long)z * g.ny + y) * g.sx;
+                f[a] = row_pair<T, 0, NC>(row, x0, g.nx, lane);
+            } else {
+                const int sm = LAY == LAY_AA_ODD ? opp_of(mirror_of(a)) : mirror_of(a);
+                const T *row = src + (long long)sm * g.plane + ((long long)zs * g.ny + y) * g.sx;
+                if (ex == 1)
+                    f[a] = row_pair<T, 1, NC>(row, x0, g.nx, lane);
+                else if (ex == -1)
+                    f[a] = row_pair<T, -1, NC>(row, x0, g.nx, lane);
+                else
+                    f[a] = row_pair<T, 0, NC>(row, x0, g.nx, lane);
+            }
+        }
+    }
+}
+
+// Store of the pair's values into one row shifted by SH (cell x goes to
+// x + SH, periodic): the counterpart of row_pair for the AA push. Interior
+// lanes store one aligned pair built with a warp shuffle; the first and last
+// lane of the warp (and the row ends) store the element that crosses into the
+// neighbouring warp's pair alone, so every element is written exactly once.
+// All 32 lanes must call it (the shuffle); lanes past the row end store nothing.
+template <typename T, int SH>
+__device__ __forceinline__ void push_row(T *row, int x0, int nx, int lane, bool valid, float2 v)
+{
+    if (SH == 0) {
+        if (valid) st2<T>(row + x0, v);
+        return;
+    }
+    if (SH == 1) {   // cells x0, x0 + 1 -> x0 + 1, x0 + 2
+        const float l = __shfl_up_sync(0xffffffffu, v.y, 1);
+        if (!valid) return;
+        if (lane == 0 || x0 == 0)
+            st<T>(row + x0 + 1, v.x);
+        else
+            st2<T>(row + x0, make_float2(l, v.x));
+        if (lane == 31 || x0 + 2 >= nx) st<T>(row + (x0 + 2 >= nx ? x0 + 2 - nx : x0 + 2), v.y);
+        return;
+    }
+    // SH == -1: cells x0, x0 + 1 -> x0 - 1, x0
+    const float r = __shfl_down_sync(0xffffffffu, v.x, 1);
+    if (!valid) return;
+    if (lane == 31 || x0 + 2 >= nx)
+        st<T>(row + x0, v.y);
+    else
+        st2<T>(row + x0, make_float2(v.y, r));
+    if (lane == 0 || x0 == 0) st<T>(row + (x0 == 0 ? nx - 1 : x0 - 1), v.x);
+}
+
+// AA odd step store of the pair: f*_a to the slot and cell of push_offset
+// (lbm_device.cuh), two cells at a time.
 template <typename T, int ROW>
-__device__ __forceinline__ void gather_pair(const T *__restrict__ src, const Geom &g, int wall, int x0, int y, int z,
-                                            int zm, int zp, int lane, float2 (&f)[Q])
+__device__ __forceinline__ void push_pair(T *dst, const Geom &g, int wall, int x0, int y, int z, int zm, int zp,
+                                          int lane, bool valid, const float2 (&f)[Q])
 {
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
         const int ex = ex_of(a), ey = ey_of(a), ez = ez_of(a);
-        const bool crosses = (ROW == ROW_BOTTOM && ey == 1) || (ROW == ROW_TOP && ey == -1);
-        const int zs = ez == 1 ? zm : (ez == -1 ? zp : z);
+        const bool crosses = (ROW == ROW_BOTTOM && ey == -1) || (ROW == ROW_TOP && ey == 1);
+        const int zt = ez == 1 ? zp : (ez == -1 ? zm : z);
         if (!crosses) {
-            const T *row = src + (long long)a * g.plane + ((long long)zs * g.ny + (y - ey)) * g.sx;
+            T *row = dst + (long long)a * g.plane + ((long long)zt * g.ny + (y + ey)) * g.sx;
             if (ex == 1)
-                f[a] = row_pair<T, 1>(row, x0, g.nx, lane);
+                push_row<T, 1>(row, x0, g.nx, lane, valid, f[a]);
             else if (ex == -1)
-                f[a] = row_pair<T, -1>(row, x0, g.nx, lane);
+                push_row<T, -1>(row, x0, g.nx, lane, valid, f[a]);
             else
-                f[a] = row_pair<T, 0>(row, x0, g.nx, lane);
+                push_row<T, 0>(row, x0, g.nx, lane, valid, f[a]);
         } else if (wall == WALL_BB) {
-            const T *row = src + (long long)opp_of(a) * g.plane + ((long long)z * g.ny + y) * g.sx;
-            f[a] = row_pair<T, 0>(row, x0, g.nx, lane);
+            T *row = dst + (long long)opp_of(a) * g.plane + ((long long)z * g.ny + y) * g.sx;
+            push_row<T, 0>(row, x0, g.nx, lane, valid, f[a]);
         } else {
-            const T *row = src + (long long)mirror_of(a) * g.plane + ((long long)zs * g.ny + y) * g.sx;
+            T *row = dst + (long long)mirror_of(a) * g.plane + ((long long)zt * g.ny + y) * g.sx;
             if (ex == 1)
-                f[a] = row_pair<T, 1>(row, x0, g.nx, lane);
+                push_row<T, 1>(row, x0, g.nx, lane, valid, f[a]);
             else if (ex == -1)
-                f[a] = row_pair<T, -1>(row, x0, g.nx, lane);
+                push_row<T, -1>(row, x0, g.nx, lane, valid, f[a]);
             else
-                f[a] = row_pair<T, 0>(row, x0, g.nx, lane);
+                push_row<T, 0>(row, x0, g.nx, lane, valid, f[a]);
         }
     }
 }
@@ -315,8 +406,11 @@ __device__ __forceinline__ PairState collide_pair(float2 (&f)[Q], const Phys &p,
 // One tile: the x-pairs xb * blockDim.x + threadIdx.x of row (y, z), i.e.
 // cells [2 xb blockDim.x, 2 (xb + 1) blockDim.x). With STATS the block writes
 // its FP64 partial sums to part_blk[0..K_PART).
-template <typename T, bool STATS, int COLL = COLL_BGK>
-__device__ __forceinline__ void pair_tile(const T *__restrict__ src, T *__restrict__ dst, const Geom &g, const Phys &p,
+//
+// LAY selects the storage scheme (LAY_PULL: src and dst are the two lattices;
+// LAY_AA_EVEN / LAY_AA_ODD: src == dst, the single AA array).
+template <typename T, bool STATS, int COLL = COLL_BGK, int LAY = LAY_PULL>
+__device__ __forceinline__ void pair_tile(const T *src, T *dst, const Geom &g, const Phys &p,
                                           float *__restrict__ tw_out, double *__restrict__ part_blk, int xb, int y,
                                           int z)
 {
@@ -328,11 +422,11 @@ __device__ __forceinline__ void pair_tile(const T *__restrict__ src, T *__restri
 
     float2 f[Q];
     if (y == 0)
-        gather_pair<T, ROW_BOTTOM>(src, g, p.wall, xl, y, z, zm, zp, lane, f);
+        gather_pair<T, ROW_BOTTOM, LAY>(src, g, p.wall, xl, y, z, zm, zp, lane, f);
     else if (y == g.ny - 1)
-        gather_pair<T, ROW_TOP>(src, g, p.wall, xl, y, z, zm, zp, lane, f);
+        gather_pair<T, ROW_TOP, LAY>(src, g, p.wall, xl, y, z, zm, zp, lane, f);
     else
-        gather_pair<T, ROW_INTERIOR>(src, g, p.wall, xl, y, z, zm, zp, lane, f);
+        gather_pair<T, ROW_INTERIOR, LAY>(src, g, p.wall, xl, y, z, zm, zp, lane, f);
 
     const PairState c = collide_pair<COLL>(f, p, row_smag(p, y, g.ny));
 
@@ -356,10 +450,17 @@ __device__ __forceinline__ void pair_tile(const T *__restrict__ src, T *__restri
             *t = make_float4(twx.x, twz.x, twx.y, twz.y);
         }
     }
-    if (valid) {
+    if (LAY == LAY_AA_ODD) {
+        if (y == 0)
+            push_pair<T, ROW_BOTTOM>(dst, g, p.wall, xl, y, z, zm, zp, lane, valid, f);
+        else if (y == g.ny - 1)
+            push_pair<T, ROW_TOP>(dst, g, p.wall, xl, y, z, zm, zp, lane, valid, f);
+        else
+            push_pair<T, ROW_INTERIOR>(dst, g, p.wall, xl, y, z, zm, zp, lane, valid, f);
+    } else if (valid) {
         T *d = dst + ((long long)z * g.ny + y) * g.sx + x0;
 #pragma unroll
-        for (int a = 0; a < Q; ++a) st2<T>(d + a * g.plane, f[a]);
+        for (int a = 0; a < Q; ++a) st2<T>(d + (LAY == LAY_AA_EVEN ? opp_of(a) : a) * g.plane, f[a]);
     }
     if (STATS) {
         double v[K_PART];
@@ -368,24 +469,8 @@ __device__ __forceinline__ void pair_tile(const T *__restrict__ src, T *__restri
         if (valid) {
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                const double r = h ? c.rho.y : c.rho.x, ux = h ? c.ux.y : c.ux.x, uy = h ? c.uy.y : c.uy.x,
-                             uz = h ? c.uz.y : c.uz.x;
-                const double tx = h ? twx.y : twx.x, tz = h ? twz.y : twz.x, m2 = tx * tx + tz * tz;
-                v[0] += r;
-                v[1] += ux;
-                v[2] += uy;
-                v[3] += uz;
-                v[4] += ux * ux;
-                v[5] += uy * uy;
-                v[6] += uz * uz;
-                v[7] += ux * uy;
-                v[8] += r * ux;
-                v[9] += r * uy;
-                v[10] += r * uz;
-                v[11] += tx;
-                v[12] += tz;
-                v[13] += sqrt(m2);
-                v[14] += m2;
+                accumulate_cell(v, h ? c.rho.y : c.rho.x, h ? c.ux.y : c.ux.x, h ? c.uy.y : c.uy.x,
+                                h ? c.uz.y : c.uz.x, h ? twx.y : twx.x, h ? twz.y : twz.x);
             }
         }
         block_reduce_store<K_PART>(v, part_blk);
@@ -414,6 +499,18 @@ __global__ void __launch_bounds__(128, LBM_PAIR_MIN_BLOCKS) k_step_pair(const T 
     const int y = blockIdx.y, z = blockIdx.z;
     const long long blk = ((long long)y * g.nz + z) * gridDim.x + blockIdx.x;
     pair_tile<T, STATS, COLL>(src, dst, g, p, tw_out, STATS ? part + blk * K_PART : nullptr, blockIdx.x, y, z);
+}
+
+// The two-cell step on the single AA array (LAY_AA_EVEN or LAY_AA_ODD).
+template <typename T, bool STATS, int COLL, int LAY>
+__global__ void __launch_bounds__(128, LBM_PAIR_MIN_BLOCKS) k_step_pair_aa(T *f, Geom g, Phys p,
+                                                                            float *__restrict__ tw_out,
+                                                                            double *__restrict__ part)
+{
+    pdl_begin();
+    const int y = blockIdx.y, z = blockIdx.z;
+    const long long blk = ((long long)y * g.nz + z) * gridDim.x + blockIdx.x;
+    pair_tile<T, STATS, COLL, LAY>(f, f, g, p, tw_out, STATS ? part + blk * K_PART : nullptr, blockIdx.x, y, z);
 }
 
 }  // namespace lbm

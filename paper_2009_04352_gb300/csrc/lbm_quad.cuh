@@ -29,16 +29,29 @@ __device__ __forceinline__ uint32_t f2h(float2 v)
 // Four halves of one source row for cells x0 .. x0 + 3 shifted by SH (cell x
 // reads x - SH), as two 32-bit words (x0, x0 + 1 | x0 + 2, x0 + 3), lower
 // element in the low half.
-template <int SH>
-__device__ __forceinline__ uint2 row_quad(const __half *__restrict__ row, int x0, int nx, int lane)
+template <bool NC>
+__device__ __forceinline__ uint2 ld_u2(const __half *p)
 {
-    const uint2 v = __ldg(reinterpret_cast<const uint2 *>(row + x0));
+    return NC ? __ldg(reinterpret_cast<const uint2 *>(p)) : *reinterpret_cast<const uint2 *>(p);
+}
+
+template <bool NC>
+__device__ __forceinline__ uint32_t ld_u16(const __half *p)
+{
+    return NC ? (uint32_t)__ldg(reinterpret_cast<const unsigned short *>(p))
+              : (uint32_t)*reinterpret_cast<const unsigned short *>(p);
+}
+
+template <int SH, bool NC = true>
+__device__ __forceinline__ uint2 row_quad(const __half *row, int x0, int nx, int lane)
+{
+    const uint2 v = ld_u2<NC>(row + x0);
     if (SH == 0) return v;
     if (SH == 1) {   // (x0 - 1, x0 | x0 + 1, x0 + 2)
         uint32_t lw = __shfl_up_sync(0xffffffffu, v.y, 1);   // (x0 - 2, x0 - 1) of the left lane
         if (lane == 0 || x0 == 0) {
             const int xl = x0 == 0 ? nx - 1 : x0 - 1;
-            lw = (uint32_t)__ldg(reinterpret_cast<const unsigned short *>(row + xl)) << 16;
+            lw = ld_u16<NC>(row + xl) << 16;
         }
         return make_uint2(__byte_perm(lw, v.x, 0x5432), __byte_perm(v.x, v.y, 0x5432));
     }
@@ -46,40 +59,122 @@ __device__ __forceinline__ uint2 row_quad(const __half *__restrict__ row, int x0
     uint32_t rw = __shfl_down_sync(0xffffffffu, v.x, 1);     // (x0 + 4, x0 + 5) of the right lane
     if (lane == 31 || x0 + 4 >= nx) {
         const int xr = x0 + 4 >= nx ? x0 + 4 - nx : x0 + 4;
-        rw = (uint32_t)__ldg(reinterpret_cast<const unsigned short *>(row + xr));
+        rw = ld_u16<NC>(row + xr);
     }
     return make_uint2(__byte_perm(v.x, v.y, 0x5432), __byte_perm(v.y, rw, 0x5432));
 }
 
-// Gather of the quad (streaming with the wall reflection of src_offset).
+// Gather of the quad (streaming with the wall reflection of src_offset); the
+// layouts as in gather_pair of lbm_pair.cuh.
+template <int ROW, int LAY = LAY_PULL>
+__device__ __forceinline__ void gather_quad(const __half *src, const Geom &g, int wall, int x0, int y, int z, int zm,
+                                            int zp, int lane, uint2 (&r)[Q])
+{
+    constexpr bool NC = LAY == LAY_PULL;
+    if constexpr (LAY == LAY_AA_EVEN) {
+        const __half *own = src + ((long long)z * g.ny + y) * g.sx + x0;
+#pragma unroll
+        for (int a = 0; a < Q; ++a) r[a] = ld_u2<false>(own + a * g.plane);
+    } else {
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            const int ex = ex_of(a), ey = ey_of(a), ez = ez_of(a);
+            const bool crosses = (ROW == ROW_BOTTOM && ey == 1) || (ROW == ROW_TOP && ey == -1);
+            const int zs = ez == 1 ? zm : (ez == -1 ? zp : z);
+            const int sa = LAY == LAY_AA_ODD ? opp_of(a) : a;
+            if (!crosses) {
+                const __half *row = src + (long long)sa * g.plane + ((long long)zs * g.ny + (y - ey)) * g.sx;
+                if (ex == 1)
+                    r[a] = row_quad<1, NC>(row, x0, g.nx, lane);
+                else if (ex == -1)
+                    r[a] = row_quad<-1, NC>(row, x0, g.nx, lane);
+                else
+                    r[a] = row_quad<0, NC>(row, x0, g.nx, lane);
+            } else if (wall == WALL_BB) {
+                const int sb = LAY == LAY_AA_ODD ? a : opp_of(a);
+                const __half *row = src + (long long)sb * g.plane + ((long long)z * g.ny + y) * g.sx;
+                r[a] = row_quad<0, NC>(row, x0, g.nx, lane);
+            } else {
+                const int sm = LAY == LAY_AA_ODD ? opp_of(mirror_of(a)) : mirror_of(a);
+                const __half *row = src + (long long)sm * g.plane + ((long long)zs * g.ny + y) * g.sx;
+                if (ex == 1)
+                    r[a] = row_quad<1, NC>(row, x0, g.nx, lane);
+                else if (ex == -1)
+                    r[a] = row_quad<-1, NC>(row, x0, g.nx, lane);
+                else
+                    r[a] = row_quad<0, NC>(row, x0, g.nx, lane);
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void st_u16(__half *p, uint32_t v) { *reinterpret_cast<unsigned short *>(p) = (unsigned short)v; }
+__device__ __forceinline__ void st_u32(__half *p, uint32_t v) { *reinterpret_cast<uint32_t *>(p) = v; }
+
+// Store of the quad's four halves into one row shifted by SH (the AA push;
+// push_row of lbm_pair.cuh for four cells). Interior lanes store one aligned
+// 8-byte word built with a shuffle and byte permutes; at the warp and row ends
+// the crossing element is stored alone. All 32 lanes must call it.
+template <int SH>
+__device__ __forceinline__ void push_row_quad(__half *row, int x0, int nx, int lane, bool valid, uint2 v)
+{
+    if (SH == 0) {
+        if (valid) *reinterpret_cast<uint2 *>(row + x0) = v;
+        return;
+    }
+    if (SH == 1) {   // cells x0 .. x0 + 3 -> x0 + 1 .. x0 + 4
+        const uint32_t lw = __shfl_up_sync(0xffffffffu, v.y, 1);   // (x0 - 2, x0 - 1) of the left lane
+        if (!valid) return;
+        if (lane == 0 || x0 == 0) {
+            st_u16(row + x0 + 1, v.x & 0xffffu);
+            st_u32(row + x0 + 2, __byte_perm(v.x, v.y, 0x5432));
+        } else {
+            *reinterpret_cast<uint2 *>(row + x0) = make_uint2(__byte_perm(lw, v.x, 0x5432), __byte_perm(v.x, v.y, 0x5432));
+        }
+        if (lane == 31 || x0 + 4 >= nx) st_u16(row + (x0 + 4 >= nx ? x0 + 4 - nx : x0 + 4), v.y >> 16);
+        return;
+    }
+    // SH == -1: cells x0 .. x0 + 3 -> x0 - 1 .. x0 + 2
+    const uint32_t rw = __shfl_down_sync(0xffffffffu, v.x, 1);   // (x0 + 4, x0 + 5) of the right lane
+    if (!valid) return;
+    if (lane == 31 || x0 + 4 >= nx) {
+        st_u32(row + x0, __byte_perm(v.x, v.y, 0x5432));
+        st_u16(row + x0 + 2, v.y >> 16);
+    } else {
+        *reinterpret_cast<uint2 *>(row + x0) = make_uint2(__byte_perm(v.x, v.y, 0x5432), __byte_perm(v.y, rw, 0x5432));
+    }
+    if (lane == 0 || x0 == 0) st_u16(row + (x0 == 0 ? nx - 1 : x0 - 1), v.x & 0xffffu);
+}
+
+// AA odd step store of the quad (push_offset of lbm_device.cuh, four cells).
 template <int ROW>
-__device__ __forceinline__ void gather_quad(const __half *__restrict__ src, const Geom &g, int wall, int x0, int y,
-                                            int z, int zm, int zp, int lane, uint2 (&r)[Q])
+__device__ __forceinline__ void push_quad(__half *dst, const Geom &g, int wall, int x0, int y, int z, int zm, int zp,
+                                          int lane, bool valid, const uint2 (&r)[Q])
 {
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
         const int ex = ex_of(a), ey = ey_of(a), ez = ez_of(a);
-        const bool crosses = (ROW == ROW_BOTTOM && ey == 1) || (ROW == ROW_TOP && ey == -1);
-        const int zs = ez == 1 ? zm : (ez == -1 ? zp : z);
+        const bool crosses = (ROW == ROW_BOTTOM && ey == -1) || (ROW == ROW_TOP && ey == 1);
+        const int zt = ez == 1 ? zp : (ez == -1 ? zm : z);
         if (!crosses) {
-            const __half *row = src + (long long)a * g.plane + ((long long)zs * g.ny + (y - ey)) * g.sx;
+            __half *row = dst + (long long)a * g.plane + ((long long)zt * g.ny + (y + ey)) * g.sx;
             if (ex == 1)
-                r[a] = row_quad<1>(row, x0, g.nx, lane);
+                push_row_quad<1>(row, x0, g.nx, lane, valid, r[a]);
             else if (ex == -1)
-                r[a] = row_quad<-1>(row, x0, g.nx, lane);
+                push_row_quad<-1>(row, x0, g.nx, lane, valid, r[a]);
             else
-                r[a] = row_quad<0>(row, x0, g.nx, lane);
+                push_row_quad<0>(row, x0, g.nx, lane, valid, r[a]);
         } else if (wall == WALL_BB) {
-            const __half *row = src + (long long)opp_of(a) * g.plane + ((long long)z * g.ny + y) * g.sx;
-            r[a] = row_quad<0>(row, x0, g.nx, lane);
+            __half *row = dst + (long long)opp_of(a) * g.plane + ((long long)z * g.ny + y) * g.sx;
+            push_row_quad<0>(row, x0, g.nx, lane, valid, r[a]);
         } else {
-            const __half *row = src + (long long)mirror_of(a) * g.plane + ((long long)zs * g.ny + y) * g.sx;
+            __half *row = dst + (long long)mirror_of(a) * g.plane + ((long long)zt * g.ny + y) * g.sx;
             if (ex == 1)
-                r[a] = row_quad<1>(row, x0, g.nx, lane);
+                push_row_quad<1>(row, x0, g.nx, lane, valid, r[a]);
             else if (ex == -1)
-                r[a] = row_quad<-1>(row, x0, g.nx, lane);
+                push_row_quad<-1>(row, x0, g.nx, lane, valid, r[a]);
             else
-                r[a] = row_quad<0>(row, x0, g.nx, lane);
+                push_row_quad<0>(row, x0, g.nx, lane, valid, r[a]);
         }
     }
 }
@@ -118,24 +213,8 @@ __device__ __forceinline__ void quad_half(uint2 (&r)[Q], const Phys &p, float sm
     if (STATS && valid) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const double rr = h ? c.rho.y : c.rho.x, ux = h ? c.ux.y : c.ux.x, uy = h ? c.uy.y : c.uy.x,
-                         uz = h ? c.uz.y : c.uz.x;
-            const double tx = h ? twx.y : twx.x, tz = h ? twz.y : twz.x, m2 = tx * tx + tz * tz;
-            v[0] += rr;
-            v[1] += ux;
-            v[2] += uy;
-            v[3] += uz;
-            v[4] += ux * ux;
-            v[5] += uy * uy;
-            v[6] += uz * uz;
-            v[7] += ux * uy;
-            v[8] += rr * ux;
-            v[9] += rr * uy;
-            v[10] += rr * uz;
-            v[11] += tx;
-            v[12] += tz;
-            v[13] += sqrt(m2);
-            v[14] += m2;
+            accumulate_cell(v, h ? c.rho.y : c.rho.x, h ? c.ux.y : c.ux.x, h ? c.uy.y : c.uy.x,
+                            h ? c.uz.y : c.uz.x, h ? twx.y : twx.x, h ? twz.y : twz.x);
         }
     }
 }
@@ -147,10 +226,10 @@ __device__ __forceinline__ void quad_half(uint2 (&r)[Q], const Phys &p, float sm
 // One tile: the x-quads xb * blockDim.x + threadIdx.x of row (y, z), i.e.
 // cells [4 xb blockDim.x, 4 (xb + 1) blockDim.x). With STATS the block writes
 // its FP64 partial sums to part_blk[0..K_PART).
-template <bool STATS, int COLL = COLL_BGK>
-__device__ __forceinline__ void quad_tile(const __half *__restrict__ src, __half *__restrict__ dst, const Geom &g,
-                                          const Phys &p, float *__restrict__ tw_out, double *__restrict__ part_blk,
-                                          int xb, int y, int z)
+template <bool STATS, int COLL = COLL_BGK, int LAY = LAY_PULL>
+__device__ __forceinline__ void quad_tile(const __half *src, __half *dst, const Geom &g, const Phys &p,
+                                          float *__restrict__ tw_out, double *__restrict__ part_blk, int xb, int y,
+                                          int z)
 {
     const int lane = threadIdx.x & 31;
     const int x0 = 4 * (xb * blockDim.x + threadIdx.x);
@@ -160,11 +239,11 @@ __device__ __forceinline__ void quad_tile(const __half *__restrict__ src, __half
 
     uint2 r[Q];
     if (y == 0)
-        gather_quad<ROW_BOTTOM>(src, g, p.wall, xl, y, z, zm, zp, lane, r);
+        gather_quad<ROW_BOTTOM, LAY>(src, g, p.wall, xl, y, z, zm, zp, lane, r);
     else if (y == g.ny - 1)
-        gather_quad<ROW_TOP>(src, g, p.wall, xl, y, z, zm, zp, lane, r);
+        gather_quad<ROW_TOP, LAY>(src, g, p.wall, xl, y, z, zm, zp, lane, r);
     else
-        gather_quad<ROW_INTERIOR>(src, g, p.wall, xl, y, z, zm, zp, lane, r);
+        gather_quad<ROW_INTERIOR, LAY>(src, g, p.wall, xl, y, z, zm, zp, lane, r);
 
     const bool wall_row = y == 0 || y == g.ny - 1;
     double v[K_PART];
@@ -176,16 +255,24 @@ __device__ __forceinline__ void quad_tile(const __half *__restrict__ src, __half
     const float smag = row_smag(p, y, g.ny);
     quad_half<0, STATS, COLL>(r, p, smag, wall_row, y == 0, twa, v, valid);
     quad_half<1, STATS, COLL>(r, p, smag, wall_row, y == 0, twb, v, valid);
-    if (valid) {
-        if (wall_row) {
-            float4 *t = reinterpret_cast<float4 *>(reinterpret_cast<float2 *>(tw_out) +
-                                                   ((long long)((y == 0 ? 0 : 1) * g.nz + z) * g.nx + x0));
-            t[0] = twa;
-            t[1] = twb;
-        }
+    if (valid && wall_row) {
+        float4 *t = reinterpret_cast<float4 *>(reinterpret_cast<float2 *>(tw_out) +
+                                               ((long long)((y == 0 ? 0 : 1) * g.nz + z) * g.nx + x0));
+        t[0] = twa;
+        t[1] = twb;
+    }
+    if (LAY == LAY_AA_ODD) {
+        if (y == 0)
+            push_quad<ROW_BOTTOM>(dst, g, p.wall, xl, y, z, zm, zp, lane, valid, r);
+        else if (y == g.ny - 1)
+            push_quad<ROW_TOP>(dst, g, p.wall, xl, y, z, zm, zp, lane, valid, r);
+        else
+            push_quad<ROW_INTERIOR>(dst, g, p.wall, xl, y, z, zm, zp, lane, valid, r);
+    } else if (valid) {
         __half *d = dst + ((long long)z * g.ny + y) * g.sx + x0;
 #pragma unroll
-        for (int a = 0; a < Q; ++a) *reinterpret_cast<uint2 *>(d + a * g.plane) = r[a];
+        for (int a = 0; a < Q; ++a)
+            *reinterpret_cast<uint2 *>(d + (LAY == LAY_AA_EVEN ? opp_of(a) : a) * g.plane) = r[a];
     }
     if (STATS) block_reduce_store<K_PART>(v, part_blk);
 }
@@ -200,6 +287,18 @@ __global__ void __launch_bounds__(128, LBM_QUAD_MIN_BLOCKS) k_step_quad(const __
     const int y = blockIdx.y, z = blockIdx.z;
     const long long blk = ((long long)y * g.nz + z) * gridDim.x + blockIdx.x;
     quad_tile<STATS, COLL>(src, dst, g, p, tw_out, STATS ? part + blk * K_PART : nullptr, blockIdx.x, y, z);
+}
+
+// The four-cell step on the single AA array (LAY_AA_EVEN or LAY_AA_ODD).
+template <bool STATS, int COLL, int LAY>
+__global__ void __launch_bounds__(128, LBM_QUAD_MIN_BLOCKS) k_step_quad_aa(__half *f, Geom g, Phys p,
+                                                                            float *__restrict__ tw_out,
+                                                                            double *__restrict__ part)
+{
+    pdl_begin();
+    const int y = blockIdx.y, z = blockIdx.z;
+    const long long blk = ((long long)y * g.nz + z) * gridDim.x + blockIdx.x;
+    quad_tile<STATS, COLL, LAY>(f, f, g, p, tw_out, STATS ? part + blk * K_PART : nullptr, blockIdx.x, y, z);
 }
 
 }  // namespace lbm

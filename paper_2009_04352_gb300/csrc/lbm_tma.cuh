@@ -230,24 +230,8 @@ __global__ void __launch_bounds__(NW * 32, 16 / NW) k_step_rows(const T *__restr
             if (STATS) {
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const double rr = h ? c.rho.y : c.rho.x, ux = h ? c.ux.y : c.ux.x, uy = h ? c.uy.y : c.uy.x,
-                                 uz = h ? c.uz.y : c.uz.x;
-                    const double tx = h ? twx.y : twx.x, tz = h ? twz.y : twz.x, m2 = tx * tx + tz * tz;
-                    v[0] += rr;
-                    v[1] += ux;
-                    v[2] += uy;
-                    v[3] += uz;
-                    v[4] += ux * ux;
-                    v[5] += uy * uy;
-                    v[6] += uz * uz;
-                    v[7] += ux * uy;
-                    v[8] += rr * ux;
-                    v[9] += rr * uy;
-                    v[10] += rr * uz;
-                    v[11] += tx;
-                    v[12] += tz;
-                    v[13] += sqrt(m2);
-                    v[14] += m2;
+                    accumulate_cell(v, h ? c.rho.y : c.rho.x, h ? c.ux.y : c.ux.x, h ? c.uy.y : c.uy.x,
+                                    h ? c.uz.y : c.uz.x, h ? twx.y : twx.x, h ? twz.y : twz.x);
                 }
             }
         }

@@ -32,7 +32,7 @@ KERNEL_AUTO, KERNEL_CELL, KERNEL_PAIR, KERNEL_TMA, KERNEL_QUAD = 0, 1, 2, 3, 4
 COLLISION_BGK, COLLISION_MRT = 0, 1
 LAW_SPALDING, LAW_LOG, LAW_POWER = 0, 1, 2
 FP32, FP16_SHIFTED = 0, 1
-PULL2 = 0
+PULL2, AA = 0, 1
 
 
 class LbmError(RuntimeError):
@@ -238,10 +238,10 @@ class Channel:
                              layout, stream, law)
 
     @classmethod
-    def from_case(cls, case, precision=FP32, wall=None, stream=None):
+    def from_case(cls, case, precision=FP32, wall=None, stream=None, layout=PULL2):
         return cls(case.nx, case.ny, case.nz, case.tau, case.cs, case.force,
                    case.wall if wall is None else wall, case.kappa, case.b_const, case.y1,
-                   case.nu_wall, case.newton_iters, precision, PULL2, stream, case.wall_law)
+                   case.nu_wall, case.newton_iters, precision, layout, stream, case.wall_law)
 
     @property
     def handle(self):
