@@ -31,12 +31,15 @@ from paper_2009_04352_gb300 import workload  # noqa: E402
 METRIC = "MLUPS and % of HBM roofline, FP32 vs FP16-storage vs batched, at stated err"
 BYTES_PER_LUP = {0: 152, 1: 76}     # 19 reads + 19 writes, FP32 / FP16 storage
 FALLBACK_HBM_GBS = 6800.0
+NOMINAL_HBM_GBS = 7900.0      # GB300 HBM3e nominal, for the second fraction
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # dominant kernel from one ncu capture of the current kernel build, keyed by
-# (workload, storage); profiles/k_step_pair_c2_256x64x128_fp32_launches.md has
-# the capture. Absent keys report null.
-NCU_TRAFFIC = {("c2", "fp32"): 264.5e6}
+# (workload, storage, layout); the captures are summarised under profiles/.
+# Absent keys report null.
+NCU_TRAFFIC = {("c2", "fp32", "pull"): 264.4e6,
+               # mean of the even and the odd AA step launch
+               ("c3", "fp16", "aa"): 1280.0e6}
 
 
 def parse():
@@ -47,10 +50,24 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16"])
+    ap.add_argument("--layout", default="pull", choices=["pull", "aa"],
+                    help="two-lattice pull (default) or the single-lattice AA layout")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
+
+
+def headline_kernel(case, precision, layout=0):
+    """Step kernel the library selects for this grid and storage (its AUTO
+    rule): the four-cell form for FP16 with nx % 4 == 0, else the two-cell form
+    for even nx, else the one-cell form; the _aa entries for the AA layout."""
+    from paper_2009_04352_gb300 import lbm
+    if precision == lbm.FP16_SHIFTED and case.nx % 4 == 0:
+        k = "k_step_quad"
+    else:
+        k = "k_step_pair" if case.nx % 2 == 0 else "k_step"
+    return k + "_aa" if layout == lbm.AA else k
 
 
 def measured_peaks():
@@ -210,7 +227,7 @@ class _Null:
         return False
 
 
-def e2e_channel(case, precision, steps, stream):
+def e2e_channel(case, precision, steps, stream, layout=0):
     """Same metric end to end through the public API with host buffers: upload
     the initial field from pinned host memory, run the steps with plane
     statistics sampled every 10 steps, read the moments and statistics back."""
@@ -223,7 +240,7 @@ def e2e_channel(case, precision, steps, stream):
     rho = torch.empty((case.nz, case.ny, case.nx), dtype=torch.float32).pin_memory().numpy()
     u = torch.empty((3, case.nz, case.ny, case.nx), dtype=torch.float32).pin_memory().numpy()
     with torch.cuda.stream(stream):
-        ch = lbm.Channel.from_case(case, precision=precision, stream=stream.cuda_stream)
+        ch = lbm.Channel.from_case(case, precision=precision, stream=stream.cuda_stream, layout=layout)
         ch.set_populations(host_f)      # warm the staging path once
         ch.step(10)
         ch.sync()
@@ -272,6 +289,20 @@ def cpu_baseline(case, budget_s=12.0):
     rec = {"value": case.cells * n / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
            "sample": f"FP64 oracle, {case.nx}x{case.ny}x{case.nz} WFB channel, {n} steps "
                      f"after 1 warm-up step ({dt:.1f} s)"}
+    # the same oracle with its planes spread over all host cores (OpenMP)
+    L = oracle.Lattice.from_case(case)
+    threads = L.set_threads(os.cpu_count() or 1)
+    L.init_channel(workload.u_mean_profile(case), workload.noise_amplitude(case), case.seed)
+    t0 = time.perf_counter()
+    L.step(1)
+    one = time.perf_counter() - t0
+    m = max(1, int(0.5 * budget_s / max(one, 1e-6)) - 1)
+    t0 = time.perf_counter()
+    L.step(m)
+    dtm = time.perf_counter() - t0
+    L.close()
+    rec["all_cores"] = {"value": case.cells * m / dtm / 1e6, "unit": "MLUPS", "cores": threads,
+                        "sample": f"same oracle, planes in parallel over {threads} threads, {m} steps ({dtm:.1f} s)"}
     return rec, u, n + 1
 
 
@@ -358,7 +389,8 @@ def main():
     if pg:
         pg.barrier()
     torch.cuda.synchronize()
-    ms, finite = time_channel(case, precision, args.steps, args.warmup, stream, clocks)
+    layout = lbm.AA if args.layout == "aa" else lbm.PULL2
+    ms, finite = time_channel(case, precision, args.steps, args.warmup, stream, clocks, layout=layout)
     torch.cuda.synchronize()
     per_gpu_mlups = case.cells * args.steps / (ms * 1e-3) / 1e6
     mlups, ms, total_cells = whole_job_rate(case.cells, args.steps, ms, pg, "cuda")
@@ -370,7 +402,7 @@ def main():
     e2e = None
     if not args.no_e2e:
         e2e_steps = min(args.steps, 2000)
-        e_ms, h2d, d2h = e2e_channel(case, precision, e2e_steps, stream)
+        e_ms, h2d, d2h = e2e_channel(case, precision, e2e_steps, stream, layout)
         e_val, e_ms, _ = whole_job_rate(case.cells, e2e_steps, e_ms, pg, "cuda")
         e2e = {"value": e_val, "unit": "MLUPS",
                "h2d_bytes_per_step": h2d / e2e_steps, "d2h_bytes_per_step": d2h / e2e_steps,
@@ -401,8 +433,8 @@ def main():
                 c = c.with_(wall_law=lbm.LAW_LOG)
             if "power" in opts:
                 c = c.with_(wall_law=lbm.LAW_POWER)
-            layout = lbm.AA if "aa" in opts else lbm.PULL2
-            vms, vfin = time_channel(c, prec, steps, 20, stream, mrt=mrt, layout=layout)
+            vlayout = lbm.AA if "aa" in opts else lbm.PULL2
+            vms, vfin = time_channel(c, prec, steps, 20, stream, mrt=mrt, layout=vlayout)
             kms = vms / steps
             gbs = BYTES_PER_LUP[prec] * c.cells / (kms * 1e-3) / 1e9
             variants[name] = {"workload": c.name, "cells": c.cells, "MLUPS": c.cells * steps / (vms * 1e-3) / 1e6,
@@ -417,13 +449,18 @@ def main():
         "data": "synthetic",
         "config": {"workload": case.name, "grid": [case.nx, case.ny, case.nz], "cells": case.cells,
                    "re_tau": case.re_tau, "tau0": case.tau, "C_s": case.cs, "wall": "wfb",
-                   "storage": args.precision, "layout": "two-lattice pull",
+                   "storage": args.precision,
+                   "layout": "single-lattice AA" if layout == lbm.AA else "two-lattice pull",
                    "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2 (129 MB): two %.0f MB lattices per step" % (
-                       BYTES_PER_LUP[precision] / 2 * case.cells / 1e6)},
+                   "l2": "inputs larger than L2 (129 MB): %s %.0f MB lattice%s per step" % (
+                       "one" if layout == lbm.AA else "two", BYTES_PER_LUP[precision] / 2 * case.cells / 1e6,
+                       "" if layout == lbm.AA else "s")},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": NCU_TRAFFIC.get((args.workload, args.precision)),
-                     "peak_source": peak_src, "kernel": "k_step", "bytes_per_lup": BYTES_PER_LUP[precision]},
+                     "frac": achieved / peak,
+                     "traffic": NCU_TRAFFIC.get((args.workload, args.precision, args.layout)),
+                     "peak_source": peak_src, "kernel": headline_kernel(case, precision, layout),
+                     "bytes_per_lup": BYTES_PER_LUP[precision],
+                     "frac_nominal": achieved / NOMINAL_HBM_GBS, "nominal_peak": NOMINAL_HBM_GBS},
         "per_gpu_MLUPS": per_gpu_mlups, "finite": finite,
         "gpu_launches": args.steps,
         "clocks": clocks.summary(),

@@ -33,6 +33,7 @@
 #ifndef LBM_H
 #define LBM_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -152,6 +153,27 @@ typedef struct lbm_handle lbm_handle;
 int lbm_create(lbm_grid g, double tau, double C_s, const double force[3],
                lbm_wall_model wm, int precision, int layout, void *cuda_stream,
                lbm_handle **out);
+
+/* Bytes of one population lattice of grid g stored at `precision`: 19 planes of
+ * ny * nz rows, each row padded to a multiple of 32 cells. 0 for an invalid
+ * grid or precision. Host arithmetic only. (No counterpart in the paper: the
+ * storage is this library's.) */
+size_t lbm_population_bytes(lbm_grid g, int precision);
+
+/* lbm_create on population arrays the caller owns, for example tensors of a
+ * framework's caching allocator, so that the big arrays come out of the
+ * caller's memory pool. pop0 (and pop1 for LBM_PULL2; NULL for LBM_AA) are
+ * device pointers on the current device, at least 16-byte aligned, each of
+ * lbm_population_bytes(g, precision) bytes. The handle reads and writes them
+ * on its stream until lbm_destroy, which does not free them; the caller keeps
+ * them alive until then and does not touch them while steps are in flight.
+ * Their contents are undefined until lbm_init_channel or lbm_set_populations.
+ * The library still allocates its small wall, statistics and partial-sum
+ * buffers. Other arguments and errors as lbm_create; a NULL pop0, a wrong
+ * pop1 for the layout or a misaligned pointer give LBM_ERR_ARG. */
+int lbm_create_from_buffers(lbm_grid g, double tau, double C_s, const double force[3],
+                            lbm_wall_model wm, int precision, int layout, void *cuda_stream,
+                            void *pop0, void *pop1, lbm_handle **out);
 
 /* Seeded channel initial field: f = f^eq(rho = 1, u0) (second-order D3Q19
  * equilibrium) with u0_x = u_mean_x[y] + a (2 U_0 - 1), u0_y = a (2 U_1 - 1),

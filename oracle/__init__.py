@@ -33,14 +33,15 @@ K_STATS = 11
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain -O2, no FMA contraction, no fast-math)."""
+    """Compile the oracle with gcc (plain -O2, no FMA contraction, no fast-math;
+    OpenMP for the all-cores timing mode where the compiler has it)."""
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or \
             os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-               "-shared", "-o", tmp, _SRC, "-lm"]
-        subprocess.run(cmd, check=True)
+        base = ["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-o", tmp, _SRC]
+        if subprocess.run(base[:-3] + ["-fopenmp"] + base[-3:] + ["-lm"], capture_output=True).returncode != 0:
+            subprocess.run(base + ["-lm"], check=True)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -96,6 +97,7 @@ def _load():
             "or_collide_mrt_rates": (None, [dp, C.c_double, C.c_double, dp, C.c_double, dp, dp, dp, dp, dp]),
             "or_van_driest": (C.c_double, [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double]),
             "or_set_les": (None, [vp, C.c_int, C.c_double, C.c_double]),
+            "or_set_threads": (C.c_int, [vp, C.c_int]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -345,6 +347,11 @@ class Lattice:
 
     def step(self, n=1):
         self._lib.or_step(self._h, int(n))
+
+    def set_threads(self, threads):
+        """All-cores timing mode (threads > 1): unsampled steps run their planes
+        in parallel. Returns the thread count in use (1 without OpenMP)."""
+        return int(self._lib.or_set_threads(self._h, int(threads)))
 
     def set_wall_law(self, law):
         """Wall function of the WFB layer: 0 Spalding, 1 log law, 2 power law."""

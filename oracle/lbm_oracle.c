@@ -433,6 +433,7 @@ typedef struct {
     int collision;              /* 0 BGK, 1 MRT */
     double vd_utau, vd_aplus;   /* van Driest reference u_tau and A+ (A+ <= 0: off) */
     int law;                    /* wall function: 0 Spalding, 1 log law, 2 power law */
+    int threads;                /* > 1: the all-cores timing mode of or_step */
     double *f, *g;              /* current and next populations [19][n] */
     double *tw;                 /* wall stress of the last step [2][nz][nx][2] */
     double *dfw;                /* Eq. B-1 per wall of the last step [2] */
@@ -598,80 +599,105 @@ void or_set_les(or_lattice *L, int collision, double u_tau, double a_plus)
  *   free-slip:   as WFB with tau_w = 0.
  * The wall stress reported for bounce-back is the tangential momentum the
  * reflection adds, -2 sum over wall-bound a of e_a,t f*_a. */
-void or_step(or_lattice *L, int nsteps)
+/* One cell of one step: collide, wall treatment, stream into L->g; adds the
+ * cell's Eq. B-1 difference to dfsum[wall] and, on sampled steps, its moments
+ * to the plane statistics. */
+static void or_cell(or_lattice *L, int x, int y, int z, int sample, double *dfsum)
 {
     const int nx = L->nx, ny = L->ny, nz = L->nz;
     const long long n = L->n;
+    long long i = cidx(L, x, y, z);
+    double f[Q], fs[Q], rho, u[3], tau;
+    for (int a = 0; a < Q; ++a) f[a] = L->f[a * n + i];
+    double damp = 1.0;
+    if (L->vd_aplus > 0.0) damp = or_van_driest(y, ny, L->vd_utau, L->nu, L->vd_aplus);
+    if (L->collision == 1)
+        or_collide_mrt(f, L->tau0, L->cs, L->F, damp, fs, &rho, u, &tau);
+    else
+        or_collide(f, L->tau0, L->cs * damp, L->F, fs, &rho, u, &tau);
+
+    int wall_id = (y == 0) ? 0 : ((y == ny - 1) ? 1 : -1);
+    double tw[2] = {0.0, 0.0};
+    if (wall_id >= 0 && L->wall == 1)
+        or_wfb_stress_law(L->law, rho, u, L->kappa, L->B, L->y1, L->nu, tw);
+    if (wall_id >= 0 && L->wall == 0) {
+        /* momentum the bounce-back returns to the fluid */
+        int dir = (wall_id == 0) ? -1 : 1;
+        for (int a = 0; a < Q; ++a)
+            if (E[a][1] == dir) {
+                tw[0] += -2.0 * E[a][0] * fs[a];
+                tw[1] += -2.0 * E[a][2] * fs[a];
+            }
+    }
+    if (wall_id >= 0) {
+        double *t = L->tw + ((size_t)(wall_id * nz + z) * nx + x) * 2;
+        t[0] = tw[0];
+        t[1] = tw[1];
+    }
+
+    if (sample) {
+        double *st = L->stats + (size_t)y * K_STATS;
+        st[0] += rho;
+        st[1] += u[0]; st[2] += u[1]; st[3] += u[2];
+        st[4] += u[0] * u[0]; st[5] += u[1] * u[1]; st[6] += u[2] * u[2];
+        st[7] += u[0] * u[1];
+        st[8] += rho * u[0]; st[9] += rho * u[1]; st[10] += rho * u[2];
+        if (wall_id >= 0) {
+            double m2 = tw[0] * tw[0] + tw[1] * tw[1];
+            double *ws = L->wstats + 4 * wall_id;
+            ws[0] += tw[0]; ws[1] += tw[1]; ws[2] += sqrt(m2); ws[3] += m2;
+        }
+    }
+
+    /* stream */
+    double out_sum = 0.0, back_sum = 0.0;
+    for (int a = 0; a < Q; ++a) {
+        int ty = y + E[a][1];
+        if (ty >= 0 && ty < ny) {
+            int tx = wrap(x + E[a][0], nx), tz = wrap(z + E[a][2], nz);
+            L->g[a * n + cidx(L, tx, ty, tz)] = fs[a];
+        } else if (L->wall == 0) {
+            L->g[opposite(a) * n + i] = fs[a];
+        } else {
+            int tx = wrap(x + E[a][0], nx), tz = wrap(z + E[a][2], nz);
+            double corr = 0.0;
+            if (L->wall == 1) corr = 0.5 * (tw[0] * E[a][0] + tw[1] * E[a][2]);
+            double v = fs[a] + corr;
+            L->g[mirror_y(a) * n + cidx(L, tx, y, tz)] = v;
+            out_sum += fs[a];
+            back_sum += v;
+        }
+    }
+    if (wall_id >= 0) dfsum[wall_id] += back_sum - out_sum;
+}
+
+void or_step(or_lattice *L, int nsteps)
+{
+    const int nx = L->nx, ny = L->ny, nz = L->nz;
     for (int s = 0; s < nsteps; ++s) {
         int sample = L->stats_every > 0 && (L->step % L->stats_every) == 0;
         double dfsum[2] = {0.0, 0.0};
-        for (int z = 0; z < nz; ++z)
-            for (int y = 0; y < ny; ++y)
-                for (int x = 0; x < nx; ++x) {
-                    long long i = cidx(L, x, y, z);
-                    double f[Q], fs[Q], rho, u[3], tau;
-                    for (int a = 0; a < Q; ++a) f[a] = L->f[a * n + i];
-                    double damp = 1.0;
-                    if (L->vd_aplus > 0.0) damp = or_van_driest(y, ny, L->vd_utau, L->nu, L->vd_aplus);
-                    if (L->collision == 1)
-                        or_collide_mrt(f, L->tau0, L->cs, L->F, damp, fs, &rho, u, &tau);
-                    else
-                        or_collide(f, L->tau0, L->cs * damp, L->F, fs, &rho, u, &tau);
-
-                    int wall_id = (y == 0) ? 0 : ((y == ny - 1) ? 1 : -1);
-                    double tw[2] = {0.0, 0.0};
-                    if (wall_id >= 0 && L->wall == 1)
-                        or_wfb_stress_law(L->law, rho, u, L->kappa, L->B, L->y1, L->nu, tw);
-                    if (wall_id >= 0 && L->wall == 0) {
-                        /* momentum the bounce-back returns to the fluid */
-                        int dir = (wall_id == 0) ? -1 : 1;
-                        for (int a = 0; a < Q; ++a)
-                            if (E[a][1] == dir) {
-                                tw[0] += -2.0 * E[a][0] * fs[a];
-                                tw[1] += -2.0 * E[a][2] * fs[a];
-                            }
-                    }
-                    if (wall_id >= 0) {
-                        double *t = L->tw + ((size_t)(wall_id * nz + z) * nx + x) * 2;
-                        t[0] = tw[0];
-                        t[1] = tw[1];
-                    }
-
-                    if (sample) {
-                        double *st = L->stats + (size_t)y * K_STATS;
-                        st[0] += rho;
-                        st[1] += u[0]; st[2] += u[1]; st[3] += u[2];
-                        st[4] += u[0] * u[0]; st[5] += u[1] * u[1]; st[6] += u[2] * u[2];
-                        st[7] += u[0] * u[1];
-                        st[8] += rho * u[0]; st[9] += rho * u[1]; st[10] += rho * u[2];
-                        if (wall_id >= 0) {
-                            double m2 = tw[0] * tw[0] + tw[1] * tw[1];
-                            double *ws = L->wstats + 4 * wall_id;
-                            ws[0] += tw[0]; ws[1] += tw[1]; ws[2] += sqrt(m2); ws[3] += m2;
-                        }
-                    }
-
-                    /* stream */
-                    double out_sum = 0.0, back_sum = 0.0;
-                    for (int a = 0; a < Q; ++a) {
-                        int ty = y + E[a][1];
-                        if (ty >= 0 && ty < ny) {
-                            int tx = wrap(x + E[a][0], nx), tz = wrap(z + E[a][2], nz);
-                            L->g[a * n + cidx(L, tx, ty, tz)] = fs[a];
-                        } else if (L->wall == 0) {
-                            L->g[opposite(a) * n + i] = fs[a];
-                        } else {
-                            int tx = wrap(x + E[a][0], nx), tz = wrap(z + E[a][2], nz);
-                            double corr = 0.0;
-                            if (L->wall == 1) corr = 0.5 * (tw[0] * E[a][0] + tw[1] * E[a][2]);
-                            double v = fs[a] + corr;
-                            L->g[mirror_y(a) * n + cidx(L, tx, y, tz)] = v;
-                            out_sum += fs[a];
-                            back_sum += v;
-                        }
-                    }
-                    if (wall_id >= 0) dfsum[wall_id] += back_sum - out_sum;
-                }
+        if (L->threads > 1 && !sample) {
+            /* all-cores timing mode: planes z in parallel (each target slot is
+             * written by exactly one source cell), the Eq. B-1 sums per plane
+             * added up in plane order afterwards */
+            double *dfz = (double *)calloc((size_t)2 * nz, sizeof(double));
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(L->threads)
+#endif
+            for (int z = 0; z < nz; ++z)
+                for (int y = 0; y < ny; ++y)
+                    for (int x = 0; x < nx; ++x) or_cell(L, x, y, z, 0, dfz + 2 * z);
+            for (int z = 0; z < nz; ++z) {
+                dfsum[0] += dfz[2 * z];
+                dfsum[1] += dfz[2 * z + 1];
+            }
+            free(dfz);
+        } else {
+            for (int z = 0; z < nz; ++z)
+                for (int y = 0; y < ny; ++y)
+                    for (int x = 0; x < nx; ++x) or_cell(L, x, y, z, sample, dfsum);
+        }
         L->dfw[0] = dfsum[0] / ((double)nx * nz);
         L->dfw[1] = dfsum[1] / ((double)nx * nz);
         if (sample) L->nsamples += 1;
@@ -680,4 +706,18 @@ void or_step(or_lattice *L, int nsteps)
         L->g = tmp;
         L->step += 1;
     }
+}
+
+/* Threads of the all-cores mode (1, the default, is the plain serial oracle;
+ * without OpenMP support at build time the loop runs serially anyway).
+ * Returns the number that will be used. */
+int or_set_threads(or_lattice *L, int threads)
+{
+#ifdef _OPENMP
+    L->threads = threads > 1 ? threads : 1;
+#else
+    (void)threads;
+    L->threads = 1;
+#endif
+    return L->threads;
 }

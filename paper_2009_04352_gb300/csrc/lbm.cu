@@ -399,7 +399,10 @@ int lbm_create_handle(lbm_grid g, double tau, double C_s, const double force[3],
         return fail(LBM_ERR_ARG, "WFB needs kappa > 0 and y1 > 0");
     if (precision != LBM_FP32 && precision != LBM_FP16_SHIFTED) return fail(LBM_ERR_ARG, "unknown precision");
     if (layout != LBM_PULL2 && layout != LBM_AA) return fail(LBM_ERR_ARG, "unknown layout");
-    if (layout == LBM_AA && pop0) return fail(LBM_ERR_ARG, "batch members use the two-lattice layout");
+    if (pop0 && layout == LBM_PULL2 && !pop1) return fail(LBM_ERR_ARG, "the two-lattice layout needs two buffers");
+    if (pop0 && layout == LBM_AA && pop1) return fail(LBM_ERR_ARG, "the AA layout takes one buffer (pop1 NULL)");
+    if ((pop0 && ((uintptr_t)pop0 & 15)) || (pop1 && ((uintptr_t)pop1 & 15)))
+        return fail(LBM_ERR_ARG, "population buffers must be 16-byte aligned");
     const int sx = (g.nx + 31) / 32 * 32;
     const long long plane = (long long)sx * g.ny * g.nz;
     if (plane > 2147483647LL) return fail(LBM_ERR_ARG, "grid too large (row-padded cells > 2^31 - 1)");
@@ -479,12 +482,12 @@ int lbm_create_handle(lbm_grid g, double tau, double C_s, const double force[3],
     if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess)
         return bail(fail(LBM_ERR_CUDA, "cannot create capture stream"));
     const size_t bytes = (size_t)lbm::Q * plane * elem_size(h);
-    h->member = pop0 != nullptr;
-    if (h->member) {
+    h->borrowed = pop0 != nullptr;
+    if (h->borrowed) {
         h->f[0] = pop0;
         h->f[1] = pop1;
     }
-    for (int i = 0; i < (layout == LBM_AA ? 1 : 2) && !h->member; ++i) {
+    for (int i = 0; i < (layout == LBM_AA ? 1 : 2) && !h->borrowed; ++i) {
         if (cudaMalloc(&h->f[i], bytes) != cudaSuccess) {
             cudaGetLastError();
             return bail(fail(LBM_ERR_OOM, "cannot allocate %zu bytes of populations", bytes));
@@ -532,7 +535,7 @@ void lbm_free_handle(lbm_handle *h)
     if (h->stream || h->f[0]) cudaStreamSynchronize(h->stream);
     for (int i = 0; i < 2; ++i) {
         if (h->chunk[i]) cudaGraphExecDestroy(h->chunk[i]);
-        if (h->f[i] && !h->member) cudaFree(h->f[i]);
+        if (h->f[i] && !h->borrowed) cudaFree(h->f[i]);
     }
     if (h->part) cudaFree(h->part);
     if (h->tw) cudaFree(h->tw);
@@ -548,6 +551,22 @@ int lbm_create(lbm_grid g, double tau, double C_s, const double force[3], lbm_wa
                int layout, void *cuda_stream, lbm_handle **out)
 {
     return lbm_create_handle(g, tau, C_s, force, wm, precision, layout, cuda_stream, nullptr, nullptr, out);
+}
+
+size_t lbm_population_bytes(lbm_grid g, int precision)
+{
+    if (g.nx < 1 || g.ny < 1 || g.nz < 1) return 0;
+    if (precision != LBM_FP32 && precision != LBM_FP16_SHIFTED) return 0;
+    const size_t sx = (size_t)(g.nx + 31) / 32 * 32;
+    return (size_t)lbm::Q * sx * g.ny * g.nz * (precision == LBM_FP16_SHIFTED ? 2 : 4);
+}
+
+int lbm_create_from_buffers(lbm_grid g, double tau, double C_s, const double force[3], lbm_wall_model wm,
+                            int precision, int layout, void *cuda_stream, void *pop0, void *pop1, lbm_handle **out)
+{
+    if (out) *out = nullptr;
+    if (!pop0) return fail(LBM_ERR_ARG, "pop0 is NULL");
+    return lbm_create_handle(g, tau, C_s, force, wm, precision, layout, cuda_stream, pop0, pop1, out);
 }
 
 int lbm_init_channel(lbm_handle *h, const double *u_mean_x, double noise_amp, uint64_t seed)

@@ -326,6 +326,7 @@ int lbm_batch_create(int n, const lbm_member *members, int precision, void *cuda
         const int rc = lbm_create_handle(m.grid, m.tau, m.C_s, m.force, m.wall, precision, LBM_PULL2, cuda_stream, base,
                                          second, &h);
         if (rc != LBM_OK) return bail(rc);
+        h->member = true;
         b->members.push_back(h);
     }
     if (cudaMalloc((void **)&b->d_inst, sizeof(BatchInst) * n) != cudaSuccess) {

@@ -32,7 +32,8 @@ struct lbm_handle {
     int tma_smem;                // dynamic shared memory bytes of the row-pipelined kernel
     int *err;                    // device flag set by a timed-out pipeline wait
     cudaGraphExec_t chunk[2];    // kGraphSteps plain steps starting from cur = 0 / 1
-    bool member;                 // member view of a batch: populations owned by the batch
+    bool member;                 // member view of a batch (stepped by the batch)
+    bool borrowed;               // population arrays owned by the caller or a batch, not freed here
     double nu_wall;              // viscosity of the wall law and of the van Driest y+
 };
 
@@ -48,8 +49,9 @@ inline int lbm_state_map(const lbm_handle *h)
 // and the van Driest factor (u_tau > 0 and a_plus > 0, else no damping).
 int lbm_apply_les(lbm_handle *h, int collision, double u_tau, double a_plus);
 
-// Create a handle; with pop0/pop1 non-NULL it is a member view whose two
-// lattices live in a batch pool (nothing is allocated for them).
+// Create a handle; with pop0 non-NULL its population arrays are borrowed
+// (a batch pool or caller buffers; nothing is allocated or freed for them).
+// pop1 is the second lattice of the two-lattice layout (NULL for AA).
 int lbm_create_handle(lbm_grid g, double tau, double C_s, const double force[3], lbm_wall_model wm, int precision,
                       int layout, void *cuda_stream, void *pop0, void *pop1, lbm_handle **out);
 

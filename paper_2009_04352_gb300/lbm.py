@@ -65,6 +65,9 @@ _VP = C.c_void_p
 _SIGNATURES = {
     "lbm_create": (C.c_int, [lbm_grid, C.c_double, C.c_double, _DP, lbm_wall_model, C.c_int, C.c_int,
                              _VP, C.POINTER(_VP)]),
+    "lbm_population_bytes": (C.c_size_t, [lbm_grid, C.c_int]),
+    "lbm_create_from_buffers": (C.c_int, [lbm_grid, C.c_double, C.c_double, _DP, lbm_wall_model, C.c_int,
+                                          C.c_int, _VP, _VP, _VP, C.POINTER(_VP)]),
     "lbm_init_channel": (C.c_int, [_VP, _DP, C.c_double, C.c_uint64]),
     "lbm_set_populations": (C.c_int, [_VP, _DP]),
     "lbm_populations": (C.c_int, [_VP, _DP]),
@@ -152,6 +155,23 @@ def lbm_create(nx, ny, nz, tau, cs, force, wall=WALL_WFB, kappa=0.41, B=5.5, y1=
     return out
 
 
+def lbm_population_bytes(nx, ny, nz, precision=FP32):
+    return int(lib().lbm_population_bytes(lbm_grid(int(nx), int(ny), int(nz)), int(precision)))
+
+
+def lbm_create_from_buffers(nx, ny, nz, tau, cs, force, pop0, pop1, wall=WALL_WFB, kappa=0.41, B=5.5, y1=1.0,
+                            nu=-1.0, newton_iters=12, precision=FP32, layout=PULL2, stream=None, law=LAW_SPALDING):
+    """pop0, pop1: device addresses (ints) of caller-owned population arrays."""
+    g = lbm_grid(int(nx), int(ny), int(nz))
+    wm = lbm_wall_model(int(wall), float(kappa), float(B), float(y1), float(nu), int(newton_iters), int(law))
+    fvec = np.ascontiguousarray(np.asarray(force, dtype=np.float64).reshape(3))
+    out = C.c_void_p()
+    s = _current_stream() if stream is None else C.c_void_p(stream)
+    _check(lib().lbm_create_from_buffers(g, float(tau), float(cs), _dp(fvec), wm, int(precision), int(layout), s,
+                                         C.c_void_p(pop0), C.c_void_p(pop1), C.byref(out)))
+    return out
+
+
 def lbm_init_channel(h, u_mean_x, noise_amp, seed):
     um = np.ascontiguousarray(np.asarray(u_mean_x, dtype=np.float64))
     _check(lib().lbm_init_channel(h, _dp(um), float(noise_amp), C.c_uint64(int(seed))))
@@ -236,6 +256,26 @@ class Channel:
         self.precision = precision
         self._h = lbm_create(nx, ny, nz, tau, cs, force, wall, kappa, B, y1, nu, newton_iters, precision,
                              layout, stream, law)
+
+    @classmethod
+    def from_buffers(cls, case, buffers, precision=FP32, wall=None, stream=None, layout=PULL2):
+        """A channel whose population arrays are caller-owned device tensors
+        (one for AA, two for the two-lattice layout), each of at least
+        lbm_population_bytes bytes; the channel keeps them referenced."""
+        self = cls.__new__(cls)
+        self.nx, self.ny, self.nz = case.nx, case.ny, case.nz
+        self.n = self.nx * self.ny * self.nz
+        self.precision = precision
+        need = lbm_population_bytes(case.nx, case.ny, case.nz, precision)
+        for t in buffers:
+            if not t.is_cuda or t.numel() * t.element_size() < need:
+                raise ValueError(f"each population buffer must be a CUDA tensor of >= {need} bytes")
+        ptrs = [t.data_ptr() for t in buffers] + [None] * (2 - len(buffers))
+        self._buffers = tuple(buffers)
+        self._h = lbm_create_from_buffers(case.nx, case.ny, case.nz, case.tau, case.cs, case.force, ptrs[0], ptrs[1],
+                                          case.wall if wall is None else wall, case.kappa, case.b_const, case.y1,
+                                          case.nu_wall, case.newton_iters, precision, layout, stream, case.wall_law)
+        return self
 
     @classmethod
     def from_case(cls, case, precision=FP32, wall=None, stream=None, layout=PULL2):

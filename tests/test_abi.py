@@ -78,3 +78,27 @@ def test_null_handle_calls_fail_cleanly():
     assert L.lbm_sync(None) == lbm.LBM_ERR_ARG
     assert L.lbm_get_step(None) == -1
     L.lbm_destroy(None)
+
+
+def test_population_bytes_host_arithmetic():
+    from paper_2009_04352_gb300 import lbm
+    # rows padded to a multiple of 32 cells, 19 planes
+    assert lbm.lbm_population_bytes(64, 32, 32, lbm.FP32) == 19 * 64 * 32 * 32 * 4
+    assert lbm.lbm_population_bytes(37, 6, 5, lbm.FP32) == 19 * 64 * 6 * 5 * 4
+    assert lbm.lbm_population_bytes(33, 2, 3, lbm.FP16_SHIFTED) == 19 * 64 * 2 * 3 * 2
+    assert lbm.lbm_population_bytes(0, 2, 3, lbm.FP32) == 0
+    assert lbm.lbm_population_bytes(8, 8, 8, 7) == 0
+
+
+def test_create_from_buffers_rejects_bad_buffers_without_device():
+    from paper_2009_04352_gb300 import lbm
+    bad = [dict(pop0=None, pop1=None, layout=lbm.PULL2),          # no buffer
+           dict(pop0=4096, pop1=None, layout=lbm.PULL2),          # two-lattice needs two
+           dict(pop0=4096, pop1=8192, layout=lbm.AA),             # AA takes one
+           dict(pop0=4104, pop1=8192, layout=lbm.PULL2),          # misaligned
+           dict(pop0=4096, pop1=8200, layout=lbm.PULL2)]
+    for kw in bad:
+        with pytest.raises(lbm.LbmError) as ei:
+            lbm.lbm_create_from_buffers(8, 8, 8, 0.6, 0.1, (1e-6, 0, 0), kw["pop0"], kw["pop1"],
+                                        layout=kw["layout"], stream=0)
+        assert ei.value.code == lbm.LBM_ERR_ARG

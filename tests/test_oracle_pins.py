@@ -645,3 +645,18 @@ def test_lattice_wall_law_stress_and_budget(oracle_lib, law):
             assert abs((p1[c] - p0[c]) - expect) <= 1e-13 + 1e-9 * abs(expect)
     with pytest.raises(ValueError):
         L.set_wall_law(3)
+
+
+def test_all_cores_mode_matches_serial(oracle_lib):
+    """The all-cores timing mode runs the same cell updates (only the order of
+    the planes changes), so its state is bitwise the serial oracle's; sampled
+    steps fall back to the serial loop."""
+    out = []
+    for threads in (1, 4):
+        L = _seeded(oracle_lib, 12, 8, 10, 1, amp=6e-3, stats_every=3)
+        L.set_threads(threads)
+        L.step(7)
+        out.append((L.populations(), L.wall_stress(), L.plane_stats()[0]))
+        L.close()
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)
