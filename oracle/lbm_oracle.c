@@ -428,7 +428,7 @@ typedef struct {
     int nx, ny, nz;
     long long n;                /* cells */
     double tau0, cs, F[3];
-    int wall;                   /* 0 bounce-back, 1 WFB, 2 free-slip */
+    int wall;                   /* 0 bounce-back, 1 WFB, 2 free-slip, 3 wall-node WFB */
     double kappa, B, y1, nu;
     int collision;              /* 0 BGK, 1 MRT */
     double vd_utau, vd_aplus;   /* van Driest reference u_tau and A+ (A+ <= 0: off) */
@@ -459,7 +459,8 @@ static int wrap(int i, int n)
 or_lattice *or_create(int nx, int ny, int nz, double tau0, double cs, const double *F,
                       int wall, double kappa, double B, double y1, double nu, int stats_every)
 {
-    if (nx < 1 || ny < 2 || nz < 1 || tau0 <= 0.5 || wall < 0 || wall > 2) return NULL;
+    if (nx < 1 || ny < 2 || nz < 1 || tau0 <= 0.5 || wall < 0 || wall > 3) return NULL;
+    if (wall == 3 && ny < 3) return NULL;   /* two wall nodes and at least one fluid layer */
     or_lattice *L = (or_lattice *)calloc(1, sizeof(or_lattice));
     L->nx = nx; L->ny = ny; L->nz = nz;
     L->n = (long long)nx * ny * nz;
@@ -590,15 +591,32 @@ void or_set_les(or_lattice *L, int collision, double u_tau, double a_plus)
     L->vd_aplus = a_plus;
 }
 
-/* One time step t -> t+1: for every cell collide (Eq. 1), find the wall
- * stress of wall-layer cells, then stream each post-collision population to
- * x + e_a. A population that would cross a wall is
- *   bounce-back: returned to the same cell in the opposite direction;
- *   WFB:         reflected specularly to x + (e_x, 0, e_z) in the mirrored
- *                direction, plus (dt / 2 dy) (tau_w . e_a) (Eqs. 14a,b, 15);
- *   free-slip:   as WFB with tau_w = 0.
- * The wall stress reported for bounce-back is the tangential momentum the
- * reflection adds, -2 sum over wall-bound a of e_a,t f*_a. */
+/* Full-way (wall-node) WFB at the wall node (x, y, z), y = 0 or ny - 1: the
+ * literal geometry of Eq. 14 and Table 1, with wall nodes and the first fluid
+ * node one lattice spacing from the wall. tau_w is the wall law applied to the
+ * first fluid node's velocity (Eqs. 15-17 with y+ = y1 u_tau / nu, y1 = 1 for
+ * this geometry). The node sends back into the fluid the specular partners of
+ * the populations that arrived from it, plus (dt / 2 dy) (tau_w . e)
+ * (Eqs. 13, 14a,b), and reverses every other population (full-way
+ * bounce-back: axis f3 <- f4 and the in-plane and outward ones, which never
+ * reach the fluid). rho and u receive the node's own moments. */
+static void or_wall_node(const or_lattice *L, int x, int y, int z, const double *f, double *fs, double *tw,
+                         double *rho, double *u)
+{
+    const long long n = L->n;
+    const int ya = (y == 0) ? 1 : L->ny - 2;   /* the first fluid node */
+    const int into = (y == 0) ? 1 : -1;        /* e_y of the populations entering the fluid */
+    double fa[Q], rho_a, ua[3];
+    const long long ia = cidx(L, x, ya, z);
+    for (int a = 0; a < Q; ++a) fa[a] = L->f[a * n + ia];
+    or_moments_cell(fa, L->F, &rho_a, ua);
+    or_wfb_stress_law(L->law, rho_a, ua, L->kappa, L->B, L->y1, L->nu, tw);
+    for (int a = 0; a < Q; ++a) fs[a] = f[opposite(a)];
+    for (int b = 0; b < Q; ++b)
+        if (E[b][1] == into) fs[b] = f[mirror_y(b)] + 0.5 * (tw[0] * E[b][0] + tw[1] * E[b][2]);
+    or_moments_cell(f, L->F, rho, u);
+}
+
 /* One cell of one step: collide, wall treatment, stream into L->g; adds the
  * cell's Eq. B-1 difference to dfsum[wall] and, on sampled steps, its moments
  * to the plane statistics. */
@@ -609,15 +627,27 @@ static void or_cell(or_lattice *L, int x, int y, int z, int sample, double *dfsu
     long long i = cidx(L, x, y, z);
     double f[Q], fs[Q], rho, u[3], tau;
     for (int a = 0; a < Q; ++a) f[a] = L->f[a * n + i];
-    double damp = 1.0;
-    if (L->vd_aplus > 0.0) damp = or_van_driest(y, ny, L->vd_utau, L->nu, L->vd_aplus);
-    if (L->collision == 1)
-        or_collide_mrt(f, L->tau0, L->cs, L->F, damp, fs, &rho, u, &tau);
-    else
-        or_collide(f, L->tau0, L->cs * damp, L->F, fs, &rho, u, &tau);
-
     int wall_id = (y == 0) ? 0 : ((y == ny - 1) ? 1 : -1);
+    const int node = L->wall == 3 && wall_id >= 0;
     double tw[2] = {0.0, 0.0};
+    if (node) {
+        or_wall_node(L, x, y, z, f, fs, tw, &rho, u);
+    } else {
+        double damp = 1.0;
+        if (L->vd_aplus > 0.0) {
+            if (L->wall == 3) {   /* distance to the nearer wall node */
+                const double d = (y < ny - 1 - y) ? y : ny - 1 - y;
+                damp = 1.0 - exp(-d * L->vd_utau / L->nu / L->vd_aplus);
+            } else {
+                damp = or_van_driest(y, ny, L->vd_utau, L->nu, L->vd_aplus);
+            }
+        }
+        if (L->collision == 1)
+            or_collide_mrt(f, L->tau0, L->cs, L->F, damp, fs, &rho, u, &tau);
+        else
+            or_collide(f, L->tau0, L->cs * damp, L->F, fs, &rho, u, &tau);
+    }
+
     if (wall_id >= 0 && L->wall == 1)
         or_wfb_stress_law(L->law, rho, u, L->kappa, L->B, L->y1, L->nu, tw);
     if (wall_id >= 0 && L->wall == 0) {
@@ -651,12 +681,19 @@ static void or_cell(or_lattice *L, int x, int y, int z, int sample, double *dfsu
 
     /* stream */
     double out_sum = 0.0, back_sum = 0.0;
+    if (node) {   /* Eq. B-1 at a wall node: what it sends back vs what arrived */
+        const int into = (wall_id == 0) ? 1 : -1;
+        for (int a = 0; a < Q; ++a) {
+            if (E[a][1] == into) back_sum += fs[a];
+            if (E[a][1] == -into) out_sum += f[a];
+        }
+    }
     for (int a = 0; a < Q; ++a) {
         int ty = y + E[a][1];
         if (ty >= 0 && ty < ny) {
             int tx = wrap(x + E[a][0], nx), tz = wrap(z + E[a][2], nz);
             L->g[a * n + cidx(L, tx, ty, tz)] = fs[a];
-        } else if (L->wall == 0) {
+        } else if (L->wall == 0 || L->wall == 3) {
             L->g[opposite(a) * n + i] = fs[a];
         } else {
             int tx = wrap(x + E[a][0], nx), tz = wrap(z + E[a][2], nz);
@@ -671,6 +708,15 @@ static void or_cell(or_lattice *L, int x, int y, int z, int sample, double *dfsu
     if (wall_id >= 0) dfsum[wall_id] += back_sum - out_sum;
 }
 
+/* One time step t -> t+1: for every cell collide (Eq. 1), find the wall
+ * stress of wall-layer cells, then stream each post-collision population to
+ * x + e_a. A population that would cross a wall is
+ *   bounce-back: returned to the same cell in the opposite direction;
+ *   WFB:         reflected specularly to x + (e_x, 0, e_z) in the mirrored
+ *                direction, plus (dt / 2 dy) (tau_w . e_a) (Eqs. 14a,b, 15);
+ *   free-slip:   as WFB with tau_w = 0.
+ * The wall stress reported for bounce-back is the tangential momentum the
+ * reflection adds, -2 sum over wall-bound a of e_a,t f*_a. */
 void or_step(or_lattice *L, int nsteps)
 {
     const int nx = L->nx, ny = L->ny, nz = L->nz;

@@ -10,7 +10,8 @@ inside each implementation from the counter-based SplitMix64 generator
 Lattice units throughout: dx = dt = 1, c_s^2 = 1/3, rho0 = 1. The channel is
 x streamwise (periodic), y wall-normal (walls at y = -1/2 and y = ny - 1/2, so
 the half height is D = ny / 2), z spanwise (periodic), as in the paper's
-turbulent channel set-up (Sec. 3.1, Fig. 3).
+turbulent channel set-up (Sec. 3.1, Fig. 3). With wall nodes (the full-way
+form of the WFB) the layers 0 and ny - 1 are the walls and D = (ny - 1) / 2.
 
 Parameter recipe (the paper prints physical settings in Table 1 but no lattice
 values): a centreline velocity U_c = 0.04 keeps the lattice Mach number near the
@@ -33,7 +34,8 @@ NOISE_FRAC = 0.10     # uniform noise amplitude, fraction of the bulk velocity
 WALL_BB = 0
 WALL_WFB = 1
 WALL_FREESLIP = 2
-WALL_NAMES = {WALL_BB: "bb", WALL_WFB: "wfb", WALL_FREESLIP: "freeslip"}
+WALL_WFB_NODE = 3     # full-way WFB on wall nodes at layers 0 and ny - 1
+WALL_NAMES = {WALL_BB: "bb", WALL_WFB: "wfb", WALL_FREESLIP: "freeslip", WALL_WFB_NODE: "wfb_node"}
 
 
 def log_law_uplus(yplus):
@@ -79,7 +81,7 @@ class ChannelCase:
 
     @property
     def half_height(self) -> float:
-        return self.ny / 2.0
+        return (self.ny - 1) / 2.0 if self.wall == WALL_WFB_NODE else self.ny / 2.0
 
     @property
     def nu(self) -> float:
@@ -92,7 +94,10 @@ class ChannelCase:
 def u_mean_profile(case: ChannelCase) -> np.ndarray:
     """Mean streamwise velocity per wall-normal layer j (length ny), FP64."""
     j = np.arange(case.ny, dtype=np.float64)
-    d = np.minimum(j + 0.5, case.ny - j - 0.5)
+    if case.wall == WALL_WFB_NODE:   # distance to the nearer wall node (0 on the walls)
+        d = np.minimum(j, case.ny - 1 - j)
+    else:
+        d = np.minimum(j + 0.5, case.ny - j - 0.5)
     yplus = case.re_tau * d / case.half_height
     return case.u_tau * log_law_uplus(yplus)
 
@@ -105,7 +110,7 @@ def noise_amplitude(case: ChannelCase) -> float:
 def derive_channel(name, nx, ny, nz, re_tau, wall=WALL_WFB, seed=1, steps=100,
                    cs=0.1, u_centre=U_CENTRE) -> ChannelCase:
     """Channel whose tau0 and force follow from Re_tau (recipe in the module doc)."""
-    D = ny / 2.0
+    D = (ny - 1) / 2.0 if wall == WALL_WFB_NODE else ny / 2.0
     u_tau = u_centre / float(log_law_uplus(re_tau))
     nu = u_tau * D / re_tau
     tau = 0.5 + 3.0 * nu

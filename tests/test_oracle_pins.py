@@ -234,7 +234,7 @@ def _seeded(oracle_lib, nx, ny, nz, wall, tau=0.52, cs=0.1, force=(2.2e-7, 0, 0)
     return L
 
 
-@pytest.mark.parametrize("wall", [0, 1, 2])
+@pytest.mark.parametrize("wall", [0, 1, 2, 3])
 def test_mass_conserved(oracle_lib, wall):
     L = _seeded(oracle_lib, 12, 8, 10, wall)
     m0 = math.fsum(L.populations().ravel())
@@ -660,3 +660,93 @@ def test_all_cores_mode_matches_serial(oracle_lib):
         L.close()
     for a, b in zip(out[0], out[1]):
         assert np.array_equal(a, b)
+
+
+# ------------------------------------------- wall-node (full-way) WFB, Eq. 14 --
+
+def _mirror_y(f):
+    """The y-mirror image of a population field [19][nz][ny][nx]."""
+    mirror = [0, 1, 2, 4, 3, 5, 6, 13, 14, 9, 10, 18, 17, 7, 8, 15, 16, 12, 11]
+    return f[mirror][:, :, ::-1, :]
+
+
+@pytest.mark.parametrize("law", [0, 1])
+def test_wall_node_pair_rules_eq12(oracle_lib, law):
+    """At every wall node the populations sent back into the fluid carry the
+    mass of those that arrived from it (Eq. 12a) and their tangential momentum
+    plus tau_w (Eq. 12b); tau_w is the wall law at the first fluid node
+    (Eqs. 15-17, y1 = 1): opposite to its u_t, with |tau_w| = rho (|u_t|/u+)^2 and
+    (u+, y+) on the law's forward curve."""
+    e, _, _, _ = oracle_lib.table()
+    nx, ny, nz = 10, 7, 8
+    L = _seeded(oracle_lib, nx, ny, nz, 3, amp=6e-3)
+    L.set_wall_law(law)
+    L.step(2)
+    f0 = L.populations()
+    rho, u = L.moments()
+    rho = rho.reshape(nz, ny, nx)
+    u = u.reshape(3, nz, ny, nx)
+    L.step(1)
+    f1 = L.populations()
+    tw = L.wall_stress()
+    nu = (0.52 - 0.5) / 3.0
+    checked = 0
+    for w, (y, ya, into) in enumerate(((0, 1, 1), (ny - 1, ny - 2, -1))):
+        arrive = [a for a in range(19) if e[a, 1] == -into]
+        back = [b for b in range(19) if e[b, 1] == into]
+        for z in range(nz):
+            for x in range(nx):
+                fin = np.array([f0[a, z, y, x] for a in arrive])
+                fout = np.array([f1[b, (z + e[b, 2]) % nz, y + into, (x + e[b, 0]) % nx] for b in back])
+                ein = e[arrive][:, [0, 2]]
+                eout = e[back][:, [0, 2]]
+                assert abs(fout.sum() - fin.sum()) <= 1e-15                               # Eq. 12a
+                dp = eout.T @ fout - ein.T @ fin
+                # differences of O(1/36) populations: round-off ~1e-17 absolute
+                assert np.allclose(dp, tw[w, z, x], rtol=1e-12, atol=2e-16)               # Eq. 12b
+                ut = np.hypot(u[0, z, ya, x], u[2, z, ya, x])
+                t = tw[w, z, x]
+                assert np.allclose(t / np.hypot(*t), -np.array([u[0, z, ya, x], u[2, z, ya, x]]) / ut, atol=1e-12)
+                utau = math.sqrt(np.hypot(*t) / rho[z, ya, x])
+                up, yp = ut / utau, utau / nu
+                if law == 0:
+                    assert oracle_lib.spalding_yplus(up) == pytest.approx(yp, rel=1e-9)
+                else:
+                    exp_up = yp if yp <= oracle_lib.loglaw_crossing() else math.log(yp) / 0.41 + 5.5
+                    assert up == pytest.approx(exp_up, rel=1e-9)
+                checked += 1
+    assert checked == 2 * nx * nz
+
+
+@pytest.mark.parametrize("wall", [1, 3])
+def test_walls_mirror_symmetric(oracle_lib, wall):
+    """The top wall is the mirror image of the bottom wall: evolving the
+    y-mirrored field gives the y-mirror of the evolved field (to round-off of
+    the reordered sums). A sign or partner slip in either wall's rules fails."""
+    nx, ny, nz = 9, 7, 6
+    F = (2.2e-7, 0.0, -1.1e-7)
+    A = _seeded(oracle_lib, nx, ny, nz, wall, force=F, amp=6e-3)
+    f = A.populations()
+    B = oracle_lib.Lattice(nx, ny, nz, 0.52, 0.1, F, wall)
+    B.set_populations(_mirror_y(f))
+    A.step(6)
+    B.step(6)
+    fa, fb = A.populations(), B.populations()
+    assert np.max(np.abs(_mirror_y(fa) - fb)) <= 1e-14 * np.max(np.abs(fa))
+    ta, tb = A.wall_stress(), B.wall_stress()
+    assert np.allclose(ta[::-1], tb, rtol=1e-9, atol=1e-20)
+
+
+def test_wall_node_rest_state_and_ny3(oracle_lib):
+    """A channel at rest stays at rest (tau_w = 0 for u_t = 0), and the
+    narrowest wall-node channel (one fluid layer) conserves mass."""
+    L = oracle_lib.Lattice(6, 5, 4, 0.6, 0.1, (0, 0, 0), 3)
+    f0 = L.populations()
+    L.step(5)
+    # sum w is 1 only to round-off, so rest is kept to round-off
+    assert np.max(np.abs(L.populations() - f0)) <= 1e-15
+    assert np.max(np.abs(L.wall_stress())) <= 1e-25
+    L = _seeded(oracle_lib, 8, 3, 5, 3, amp=6e-3)
+    m0 = math.fsum(L.populations().ravel())
+    L.step(5)
+    assert abs(math.fsum(L.populations().ravel()) - m0) <= 1e-12 * m0
