@@ -443,10 +443,12 @@ def test_mrt_conserves_mass_and_adds_force(oracle_lib, seed):
     fs, rho, u, tau = oracle_lib.collide_mrt(f, 0.52, 0.1, F)
     assert abs(fs.sum() - f.sum()) < 1e-15
     assert np.allclose(e.T @ (fs - f), F, rtol=1e-8, atol=1e-17)
-    # the ghost moments relax toward their equilibria with the published rates
+    # the ghost moments relax with the published rates, the stress and pi
+    # moments with 1 / tau_eff
     M = oracle_lib.mrt_matrix()
     s = oracle_lib.mrt_rates(tau)
     assert s[1] == 1.19 and s[2] == 1.4 and s[4] == 1.2 and s[16] == 1.98 and s[9] == 1.0 / tau
+    assert s[10] == s[12] == 1.0 / tau
 
 
 def _shear_wave_decay(oracle_lib, collision, tau, nz=64, steps=400, amp=1e-3):
@@ -750,3 +752,34 @@ def test_wall_node_rest_state_and_ny3(oracle_lib):
     m0 = math.fsum(L.populations().ravel())
     L.step(5)
     assert abs(math.fsum(L.populations().ravel()) - m0) <= 1e-12 * m0
+
+
+def _max_amplification(oracle_lib, rates, nk=9):
+    """Largest |eigenvalue| of one linearised step (collision about rest, then
+    streaming) over plane waves exp(i k . x), k on a grid of [0, pi]^3 (von
+    Neumann analysis of the scheme)."""
+    e, w, _, _ = oracle_lib.table()
+    e = np.asarray(e, dtype=float)
+    w = np.asarray(w, dtype=float)
+    M = np.asarray(oracle_lib.mrt_matrix(), dtype=float).reshape(19, 19)
+    Minv = M.T / np.sum(M * M, axis=1)[None, :]
+    E = w[:, None] * (1 + 3 * e @ e.T)     # d f^eq / d f at rest
+    C = np.eye(19) - Minv @ np.diag(rates) @ M @ (np.eye(19) - E)
+    g = np.linspace(0, math.pi, nk)
+    ks = np.array([[a, b, c] for a in g for b in g for c in g[::2]])
+    A = np.exp(-1j * ks @ e.T)[:, :, None] * C[None]
+    return float(np.max(np.abs(np.linalg.eigvals(A))))
+
+
+def test_mrt_linearly_stable_near_half(oracle_lib):
+    """Von Neumann analysis at the channel runs' tau0 (0.5002) and closer to
+    1/2: the oracle's MRT rates amplify no plane wave (|lambda| <= 1, like BGK),
+    while the published rate set with s_pi = 1.4 does (|lambda| ~ 1.007), the
+    reason the pi moments relax with 1 / tau_eff here."""
+    for tau in (0.5002, 0.50005, 0.52, 0.8):
+        s = np.asarray(oracle_lib.mrt_rates(tau), dtype=float)
+        assert _max_amplification(oracle_lib, s) <= 1.0 + 1e-9, tau
+        assert _max_amplification(oracle_lib, np.full(19, 1.0 / tau)) <= 1.0 + 1e-9
+    s = np.asarray(oracle_lib.mrt_rates(0.5002), dtype=float)
+    s[10] = s[12] = 1.4
+    assert _max_amplification(oracle_lib, s) > 1.005
