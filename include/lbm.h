@@ -55,10 +55,25 @@ enum {
 
 typedef struct { int nx, ny, nz; } lbm_grid;
 
+/* Wall treatment of the two walls y = const.
+ *   BB, WFB, FREESLIP: halfway walls at y = -1/2 and y = ny - 1/2, every layer
+ *     is fluid (half height D = ny / 2); the WFB correction rides on the
+ *     reflected populations of the first layer.
+ *   WFB_NODE: the full-way form of the WFB with wall nodes (the geometry of
+ *     Eq. 14 and Table 1): layers 0 and ny - 1 are wall nodes, the fluid is
+ *     layers 1 .. ny - 2 (D = (ny - 1) / 2). A wall node does not collide; it
+ *     takes tau_w from the wall function at the first fluid node (y1 = its
+ *     distance, 1 in lattice units), sends back into the fluid the specular
+ *     partners of the populations that arrived from it plus (tau_w . e) / 2
+ *     (Eqs. 13, 14a,b), and reverses all others. Needs ny >= 3, the two-lattice
+ *     layout and the CELL or PAIR kernel (AUTO picks PAIR for even nx); the
+ *     moments and statistics of layers 0 and ny - 1 are those of the wall
+ *     nodes' own populations. */
 typedef enum {
     LBM_WALL_BB = 0,        /* halfway bounce-back: the no-slip reference (Sec. 2.1, Eq. 3) */
     LBM_WALL_WFB = 1,       /* wall-function bounce (Sec. 2.2, Eqs. 14-15) */
-    LBM_WALL_FREESLIP = 2   /* specular reflection (Sec. 2.1, Eq. 4); WFB with tau_w = 0 */
+    LBM_WALL_FREESLIP = 2,  /* specular reflection (Sec. 2.1, Eq. 4); WFB with tau_w = 0 */
+    LBM_WALL_WFB_NODE = 3   /* wall-function bounce on wall nodes (full-way form) */
 } lbm_wall_kind;
 
 /* Wall function that gives tau_w to the WFB layer. Sec. 2.3 uses Spalding's

@@ -61,14 +61,16 @@ int select_kernel(lbm_handle *h, int kernel)
 {
     const bool even = (h->g.nx % 2) == 0;
     const bool seg = (h->g.nx % 64) == 0;
-    const bool quad = (h->g.nx % 4) == 0 && h->precision == LBM_FP16_SHIFTED;
+    const bool node = h->p.wall == lbm::WALL_NODE;   // wall nodes: the cell and pair forms only
+    const bool quad = (h->g.nx % 4) == 0 && h->precision == LBM_FP16_SHIFTED && !node;
     // AUTO: FP16 storage with nx a multiple of 4 runs the four-cell kernel, else
     // the two-cell kernel where nx is even, else the one-cell kernel (measured
     // fastest in that order on GB300 for every benchmark grid)
     if (kernel == LBM_KERNEL_AUTO) kernel = quad ? LBM_KERNEL_QUAD : (even ? LBM_KERNEL_PAIR : LBM_KERNEL_CELL);
     if (kernel == LBM_KERNEL_PAIR && !even) return fail(LBM_ERR_ARG, "two-cell kernel needs an even nx");
     if (kernel == LBM_KERNEL_QUAD && !quad)
-        return fail(LBM_ERR_ARG, "four-cell kernel needs FP16 storage and nx a multiple of 4");
+        return fail(LBM_ERR_ARG, "four-cell kernel needs FP16 storage, nx a multiple of 4 and halfway walls");
+    if (kernel == LBM_KERNEL_TMA && node) return fail(LBM_ERR_ARG, "the pipelined kernel has no wall-node form");
     if (kernel == LBM_KERNEL_TMA && !seg) return fail(LBM_ERR_ARG, "pipelined kernel needs nx a multiple of 64");
     if (kernel == LBM_KERNEL_TMA && h->layout == LBM_AA)
         return fail(LBM_ERR_ARG, "the AA layout runs the cell, pair or quad kernel");
@@ -391,11 +393,14 @@ int lbm_create_handle(lbm_grid g, double tau, double C_s, const double force[3],
     if (!(tau > 0.5)) return fail(LBM_ERR_ARG, "tau must exceed 1/2");
     if (!(C_s >= 0.0)) return fail(LBM_ERR_ARG, "C_s must be >= 0");
     if (!force) return fail(LBM_ERR_ARG, "force is NULL");
-    if (wm.kind < LBM_WALL_BB || wm.kind > LBM_WALL_FREESLIP) return fail(LBM_ERR_ARG, "unknown wall kind");
+    if (wm.kind < LBM_WALL_BB || wm.kind > LBM_WALL_WFB_NODE) return fail(LBM_ERR_ARG, "unknown wall kind");
+    if (wm.kind == LBM_WALL_WFB_NODE && g.ny < 3) return fail(LBM_ERR_ARG, "wall nodes need ny >= 3");
+    if (wm.kind == LBM_WALL_WFB_NODE && layout == LBM_AA)
+        return fail(LBM_ERR_ARG, "wall nodes read the first fluid layer of the source lattice: two-lattice layout only");
     if (wm.law < LBM_LAW_SPALDING || wm.law > LBM_LAW_POWER) return fail(LBM_ERR_ARG, "unknown wall law");
     if (wm.law == LBM_LAW_LOG && !(wm.kappa > 0.0 && wm.B > (1.0 + log(wm.kappa)) / wm.kappa))
         return fail(LBM_ERR_ARG, "log law: y+ and ln(y+)/kappa + B never cross for these kappa, B");
-    if (wm.kind == LBM_WALL_WFB && !(wm.kappa > 0.0 && wm.y1 > 0.0))
+    if ((wm.kind == LBM_WALL_WFB || wm.kind == LBM_WALL_WFB_NODE) && !(wm.kappa > 0.0 && wm.y1 > 0.0))
         return fail(LBM_ERR_ARG, "WFB needs kappa > 0 and y1 > 0");
     if (precision != LBM_FP32 && precision != LBM_FP16_SHIFTED) return fail(LBM_ERR_ARG, "unknown precision");
     if (layout != LBM_PULL2 && layout != LBM_AA) return fail(LBM_ERR_ARG, "unknown layout");
@@ -447,7 +452,7 @@ int lbm_create_handle(lbm_grid g, double tau, double C_s, const double force[3],
     }
     h->p.t02 = (float)((double)h->p.tau0 * (double)h->p.tau0);
     h->nu_wall = nu;
-    // MRT constants: ghost rates of d'Humieres et al. (2002) and the Guo
+    // MRT constants: ghost rates after d'Humieres et al. (2002) and the Guo
     // forcing in moment space, M G = gc + gu . u with
     // G_a = w_a [3 e_a.F + (9 (e_a.u)(e_a.F) - 3 u.F)]
     h->p.collision = lbm::COLL_BGK;
@@ -455,7 +460,7 @@ int lbm_create_handle(lbm_grid g, double tau, double C_s, const double force[3],
     for (int i = 0; i < lbm::Q; ++i) {
         double r = 1.0;
         if (i == 1) r = 1.19;
-        if (i == 2 || i == 10 || i == 12) r = 1.4;
+        if (i == 2) r = 1.4;   // rows 10 and 12 relax with 1/tau_eff (mrt_stress)
         if (i == 4 || i == 6 || i == 8) r = 1.2;
         if (i >= 16) r = 1.98;
         h->p.mrt_s[i] = (float)r;

@@ -58,7 +58,11 @@ __host__ __device__ constexpr int mirror_of(int a)
 // Weights 1/3, 1/18, 1/36 (the DdQq scheme the paper cites as ref. [27]).
 __host__ __device__ constexpr double w_of(int a) { return a == 0 ? 1.0 / 3.0 : (a <= 6 ? 1.0 / 18.0 : 1.0 / 36.0); }
 
-enum { WALL_BB = 0, WALL_WFB = 1, WALL_FREESLIP = 2 };
+enum { WALL_BB = 0, WALL_WFB = 1, WALL_FREESLIP = 2, WALL_NODE = 3 };
+// Walls whose out-of-channel populations return to the own cell's opposite
+// slot: halfway bounce-back, and the wall nodes of the full-way WFB (their
+// outward populations never reach the fluid).
+__host__ __device__ constexpr bool bb_map(int wall) { return wall == WALL_BB || wall == WALL_NODE; }
 enum { ROW_INTERIOR = 0, ROW_BOTTOM = 1, ROW_TOP = 2 };
 // Step kinds: two-lattice pull, AA even step (phase 0 -> 1), AA odd step (1 -> 0).
 enum { LAY_PULL = 0, LAY_AA_EVEN = 1, LAY_AA_ODD = 2 };
@@ -144,7 +148,14 @@ __host__ __device__ constexpr int mrt_norm(int i)
 }
 
 // Moments relaxed with 1/tau_eff (the viscous stress: 3p_xx, p_ww, p_xy, p_yz, p_xz).
-__host__ __device__ constexpr bool mrt_stress(int i) { return i == 9 || i == 11 || i == 13 || i == 14 || i == 15; }
+// Rows relaxing with 1/tau_eff: the five stress moments and the two
+// fourth-order pi moments (10, 12). With the published pi rate of 1.4 the
+// scheme is linearly unstable for tau0 below about 0.502, where the channel
+// runs operate.
+__host__ __device__ constexpr bool mrt_stress(int i)
+{
+    return i == 9 || i == 10 || i == 11 || i == 12 || i == 13 || i == 14 || i == 15;
+}
 // Non-conserved moments even (odd) under e -> -e.
 __host__ __device__ constexpr bool mrt_even_ghost(int i) { return i == 1 || i == 2 || (i >= 9 && i <= 15); }
 __host__ __device__ constexpr bool mrt_odd_ghost(int i) { return i == 4 || i == 6 || i == 8 || i >= 16; }
@@ -154,7 +165,9 @@ __host__ __device__ constexpr bool mrt_odd_ghost(int i) { return i == 4 || i == 
 __device__ __forceinline__ float row_smag(const Phys &p, int y, int ny)
 {
     if (p.vd_scale <= 0.f) return p.smag;
-    const float d = fminf(y + 0.5f, ny - y - 0.5f);
+    // distance to the nearer wall: layer centre j + 1/2 (halfway walls) or j
+    // (wall nodes at layers 0 and ny - 1)
+    const float d = p.wall == WALL_NODE ? (float)min(y, ny - 1 - y) : fminf(y + 0.5f, ny - y - 0.5f);
     const float D = 1.f - expf(-d * p.vd_scale);
     return p.smag * D * D;
 }
@@ -192,7 +205,7 @@ __device__ __forceinline__ long long src_position(const Geom &g, int wall, int a
     const bool crosses = (ROW == ROW_BOTTOM && ey == 1) || (ROW == ROW_TOP && ey == -1);
     if (crosses) {
         ys = y;
-        if (wall == WALL_BB) {
+        if (bb_map(wall)) {
             xs = x;
             zs = z;
             slot = opp_of(a);
@@ -240,7 +253,7 @@ __device__ __forceinline__ long long push_offset(const Geom &g, int wall, int a,
     const bool crosses = (ROW == ROW_BOTTOM && ey == -1) || (ROW == ROW_TOP && ey == 1);
     if (crosses) {
         yt = y;
-        if (wall == WALL_BB) {
+        if (bb_map(wall)) {
             xt = x;
             zt = z;
             slot = opp_of(a);
@@ -343,15 +356,16 @@ __device__ __forceinline__ Moments moments_of(const float (&f)[Q])
 __device__ __forceinline__ float spalding_uplus(float R, const Phys &p, unsigned mask)
 {
     float up = sqrtf(R);
-    if (R > 100.f) up = fminf(up, logf(R) / p.kappa + p.B);
+    if (R > 100.f) up = fminf(up, __fadd_rn(logf(R) / p.kappa, p.B));
     for (int it = 0; it < p.newton_iters; ++it) {
         const float k = p.kappa * up;
         const float ek = expf(k);
-        const float t2 = ek - 1.f - k - 0.5f * k * k;        // e^k - 1 - k - k^2/2
-        const float t3 = t2 - k * k * k * (1.f / 6.f);      // ... - k^3/6
-        const float S = up + p.ekb * t3;                     // y+(u+)
-        const float dS = 1.f + p.ekb * p.kappa * t2;         // dy+/du+
-        const float step = (up * S - R) / (S + up * dS);
+        const float k2 = __fmul_rn(k, k);
+        const float t2 = __fsub_rn(__fsub_rn(__fsub_rn(ek, 1.f), k), __fmul_rn(0.5f, k2));   // e^k - 1 - k - k^2/2
+        const float t3 = __fsub_rn(t2, __fmul_rn(__fmul_rn(k2, k), 1.f / 6.f));            // ... - k^3/6
+        const float S = __fmaf_rn(p.ekb, t3, up);                                           // y+(u+)
+        const float dS = __fmaf_rn(__fmul_rn(p.ekb, p.kappa), t2, 1.f);                     // dy+/du+
+        const float step = __fmaf_rn(up, S, -R) / __fmaf_rn(up, dS, S);
         up -= step;
         const bool done = fabsf(step) <= 1e-7f * up;
         if (__all_sync(mask, done)) break;
@@ -368,11 +382,11 @@ __device__ __forceinline__ float loglaw_uplus(float R, const Phys &p, unsigned m
 {
     const bool visc = R <= p.law_r2;
     const float lr = logf(fmaxf(R, p.law_r2));
-    const float u0 = lr * p.ikappa + p.B;
-    float up = u0 - logf(u0) * p.ikappa;
+    const float u0 = __fmaf_rn(lr, p.ikappa, p.B);
+    float up = __fmaf_rn(-logf(u0), p.ikappa, u0);
     for (int it = 0; it < p.newton_iters; ++it) {
-        const float h = up + (logf(up) - lr) * p.ikappa - p.B;
-        const float step = h / (1.f + p.ikappa / up);
+        const float h = __fsub_rn(__fmaf_rn(__fsub_rn(logf(up), lr), p.ikappa, up), p.B);
+        const float step = h / __fadd_rn(1.f, p.ikappa / up);
         up -= step;
         const bool done = visc || fabsf(step) <= 1e-7f * up;
         if (__all_sync(mask, done)) break;

@@ -33,7 +33,7 @@ __device__ __forceinline__ CellState velocity(const Moments &m, const Phys &p)
     CellState c;
     c.rho = 1.f + m.drho;
     const float idev = -m.drho / c.rho;
-    const float jx = m.jx + 0.5f * p.Fx, jy = m.jy + 0.5f * p.Fy, jz = m.jz + 0.5f * p.Fz;
+    const float jx = __fmaf_rn(0.5f, p.Fx, m.jx), jy = __fmaf_rn(0.5f, p.Fy, m.jy), jz = __fmaf_rn(0.5f, p.Fz, m.jz);
     c.ux = fmaf(jx, idev, jx);
     c.uy = fmaf(jy, idev, jy);
     c.uz = fmaf(jz, idev, jz);
@@ -162,21 +162,58 @@ __device__ __forceinline__ CellState collide(const float (&f)[Q], float (&fs)[Q]
 // tau_w = rho u_tau^2 with u_tau = |u_t| / u+ from Spalding's law, directed
 // against the tangential velocity (Eq. 15). For bounce-back the reported stress
 // is the tangential momentum the reflection returns, -2 sum e_b,t f*_b.
+// Wall shear stress of the wall function from the state c of the cell that
+// feeds it (Eqs. 15-17): |tau_w| = rho (|u_t| / u+)^2 against u_t. The lanes
+// in `lanes` iterate the wall law together. Roundings are explicit here and in
+// the wall laws, so every kernel form computes the same tau_w.
+__device__ __forceinline__ void wfb_stress(const CellState &c, const Phys &p, unsigned lanes, float &twx, float &twz)
+{
+    twx = 0.f;
+    twz = 0.f;
+    const float ut = sqrtf(__fmaf_rn(c.uz, c.uz, __fmul_rn(c.ux, c.ux)));
+    const float R = fmaxf(p.y1_over_nu * ut, 1e-30f);
+    const float up = wall_uplus(R, p, lanes);
+    const float utau = ut / up;
+    const float tw = c.rho * utau * utau;
+    if (ut > 0.f) {
+        twx = -c.ux / ut * tw;
+        twz = -c.uz / ut * tw;
+    }
+}
+
+// Full-way WFB at a wall node (layer 0 or ny - 1, WALL_NODE): f holds the
+// node's gathered populations and ca the state of the first fluid node. fs
+// receives what the node sends out: for each population b entering the fluid
+// the specular partner of the one that arrived from it plus (tau_w . e_b) / 2
+// (Eqs. 13, 14a,b; the axis one unchanged), every other population reversed
+// (full-way bounce-back; those never reach the fluid).
+__device__ __forceinline__ void wall_node(const float (&f)[Q], float (&fs)[Q], const CellState &ca, const Phys &p,
+                                          bool bottom, unsigned lanes, float &twx, float &twz)
+{
+    wfb_stress(ca, p, lanes, twx, twz);
+    const float hx = 0.5f * twx, hz = 0.5f * twz;
+#pragma unroll
+    for (int a = 0; a < Q; ++a) fs[a] = f[opp_of(a)];
+    if (bottom) {
+        fs[7] = f[13] + hx;
+        fs[14] = f[8] - hx;
+        fs[11] = f[18] + hz;
+        fs[17] = f[12] - hz;
+    } else {
+        fs[13] = f[7] + hx;
+        fs[8] = f[14] - hx;
+        fs[18] = f[11] + hz;
+        fs[12] = f[17] - hz;
+    }
+}
+
 __device__ __forceinline__ void wall_layer(float (&fs)[Q], const CellState &c, const Phys &p, bool bottom,
                                            unsigned lanes, float &twx, float &twz)
 {
     twx = 0.f;
     twz = 0.f;
     if (p.wall == WALL_WFB) {
-        const float ut = sqrtf(c.ux * c.ux + c.uz * c.uz);
-        const float R = fmaxf(p.y1_over_nu * ut, 1e-30f);
-        const float up = wall_uplus(R, p, lanes);
-        const float utau = ut / up;
-        const float tw = c.rho * utau * utau;
-        if (ut > 0.f) {
-            twx = -c.ux / ut * tw;
-            twz = -c.uz / ut * tw;
-        }
+        wfb_stress(c, p, lanes, twx, twz);
         const float hx = 0.5f * twx, hz = 0.5f * twz;
         if (bottom) {
             fs[13] += hx;
@@ -273,19 +310,35 @@ __device__ __forceinline__ void cell_step(const T *src, T *dst, const Geom &g, c
         gather<T, MAP_AA0, false>(src, g, p.wall, xc, y, z, f);
     else
         gather<T, MAP_AA1, false>(src, g, p.wall, xc, y, z, f);
-    const CellState c = collide<COLL>(f, fs, p, row_smag(p, y, g.ny));
 
     float twx = 0.f, twz = 0.f;
     const bool wall_row = (y == 0) || (y == g.ny - 1);
-    if (wall_row) {
-        // lanes of this warp still running: all of them with STATS (no early
-        // exit), otherwise those with x < nx
-        unsigned lanes = 0xffffffffu;
-        if (!STATS) {
-            const int first = blockIdx.x * blockDim.x + (threadIdx.x & ~31);
-            const int nv = g.nx - first;
-            lanes = nv >= 32 ? 0xffffffffu : ((1u << nv) - 1u);
+    // lanes of this warp still running: all of them with STATS (no early
+    // exit), otherwise those with x < nx
+    unsigned lanes = 0xffffffffu;
+    if (!STATS) {
+        const int first = blockIdx.x * blockDim.x + (threadIdx.x & ~31);
+        const int nv = g.nx - first;
+        lanes = nv >= 32 ? 0xffffffffu : ((1u << nv) - 1u);
+    }
+    CellState c;
+    const bool node_row = LAY == LAY_PULL && wall_row && p.wall == WALL_NODE;
+    if (node_row) {
+        // wall node of the full-way WFB: no collision; tau_w from the first
+        // fluid node (the two-lattice source is not written during the step)
+        float fa[Q];
+        gather<T, MAP_PULL, true>(src, g, p.wall, xc, y == 0 ? 1 : g.ny - 2, z, fa);
+        const CellState ca = velocity(moments_of(fa), p);
+        c = velocity(moments_of(f), p);
+        wall_node(f, fs, ca, p, y == 0, lanes, twx, twz);
+        if (valid) {
+            float2 *t = reinterpret_cast<float2 *>(tw_out) + ((long long)((y == 0 ? 0 : 1) * g.nz + z) * g.nx + x);
+            *t = make_float2(twx, twz);
         }
+    } else {
+        c = collide<COLL>(f, fs, p, row_smag(p, y, g.ny));
+    }
+    if (wall_row && !node_row) {
         wall_layer(fs, c, p, y == 0, lanes, twx, twz);
         if (valid) {
             float2 *t = reinterpret_cast<float2 *>(tw_out) + ((long long)((y == 0 ? 0 : 1) * g.nz + z) * g.nx + x);

@@ -94,7 +94,7 @@ __device__ __forceinline__ void gather_pair(const T *src, const Geom &g, int wal
                     f[a] = row_pair<T, -1, NC>(row, x0, g.nx, lane);
                 else
                     f[a] = row_pair<T, 0, NC>(row, x0, g.nx, lane);
-            } else if (wall == WALL_BB) {
+            } else if (bb_map(wall)) {
                 const int sb = LAY == LAY_AA_ODD ? a : opp_of(a);
                 const T *row = src + (long long)sb * g.plane + ((long long)z * g.ny + y) * g.sx;
                 f[a] = row_pair<T, 0, NC>(row, x0, g.nx, lane);
@@ -164,7 +164,7 @@ __device__ __forceinline__ void push_pair(T *dst, const Geom &g, int wall, int x
                 push_row<T, -1>(row, x0, g.nx, lane, valid, f[a]);
             else
                 push_row<T, 0>(row, x0, g.nx, lane, valid, f[a]);
-        } else if (wall == WALL_BB) {
+        } else if (bb_map(wall)) {
             T *row = dst + (long long)opp_of(a) * g.plane + ((long long)z * g.ny + y) * g.sx;
             push_row<T, 0>(row, x0, g.nx, lane, valid, f[a]);
         } else {
@@ -246,12 +246,15 @@ __device__ __forceinline__ PairState collide_pair(float2 (&f)[Q], const Phys &p,
     const float2 qo = fma2(pxy, pxy, fma2(pxz, pxz, mul2(pyz, pyz)));
     const float2 q2 = add2(add2(qo, qo), fma2(pxx, pxx, fma2(pyy, pyy, mul2(pzz, pzz))));
     // omega = 1 / tau_eff = 2 / (tau0 + sqrt(tau0^2 + smag |Pi_neq| / rho)),
-    // 1/rho = 1 + idev (a sum of positive terms: no cancellation)
+    // 1/rho = 1 + idev (a sum of positive terms: no cancellation); explicit
+    // roundings, so every kernel that inlines this computes the same bits
     float2 omega;
     {
         const float t02 = p.t02;
-        const float cqx = smag * sqrtf(q2.x) * (1.f + idev.x), cqy = smag * sqrtf(q2.y) * (1.f + idev.y);
-        omega = make_float2(2.f / (p.tau0 + sqrtf(t02 + cqx)), 2.f / (p.tau0 + sqrtf(t02 + cqy)));
+        const float cqx = __fmul_rn(__fmul_rn(smag, sqrtf(q2.x)), __fadd_rn(1.f, idev.x));
+        const float cqy = __fmul_rn(__fmul_rn(smag, sqrtf(q2.y)), __fadd_rn(1.f, idev.y));
+        omega = make_float2(2.f / __fadd_rn(p.tau0, sqrtf(__fadd_rn(t02, cqx))),
+                            2.f / __fadd_rn(p.tau0, sqrtf(__fadd_rn(t02, cqy))));
     }
     if constexpr (COLL == COLL_MRT) {
         // MRT (d'Humieres et al. 2002) on the pair sums s = 2 hs and differences
@@ -420,6 +423,24 @@ __device__ __forceinline__ void pair_tile(const T *src, T *dst, const Geom &g, c
     const int xl = valid ? x0 : g.nx - 2;   // lanes past the row end read in bounds and store nothing
     const int zm = z == 0 ? g.nz - 1 : z - 1, zp = z == g.nz - 1 ? 0 : z + 1;
 
+    // wall node of the full-way WFB (two-lattice layout only): no collision;
+    // tau_w from the first fluid node, whose state is gathered first so that
+    // its populations are dead before the node's own are loaded
+    const bool node_row = LAY == LAY_PULL && p.wall == WALL_NODE && (y == 0 || y == g.ny - 1);
+    CellState ca0{}, ca1{};
+    if (node_row) {
+        float2 fa[Q];
+        gather_pair<T, ROW_INTERIOR, LAY>(src, g, p.wall, xl, y == 0 ? 1 : g.ny - 2, z, zm, zp, lane, fa);
+        float a0[Q], a1[Q];
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            a0[a] = fa[a].x;
+            a1[a] = fa[a].y;
+        }
+        ca0 = velocity(moments_of(a0), p);
+        ca1 = velocity(moments_of(a1), p);
+    }
+
     float2 f[Q];
     if (y == 0)
         gather_pair<T, ROW_BOTTOM, LAY>(src, g, p.wall, xl, y, z, zm, zp, lane, f);
@@ -428,10 +449,34 @@ __device__ __forceinline__ void pair_tile(const T *src, T *dst, const Geom &g, c
     else
         gather_pair<T, ROW_INTERIOR, LAY>(src, g, p.wall, xl, y, z, zm, zp, lane, f);
 
-    const PairState c = collide_pair<COLL>(f, p, row_smag(p, y, g.ny));
-
     float2 twx = bc(0.f), twz = bc(0.f);
-    if (y == 0 || y == g.ny - 1) {
+    PairState c;
+    if (node_row) {
+        float fa[Q], fb[Q], oa[Q], ob[Q];
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            fa[a] = f[a].x;
+            fb[a] = f[a].y;
+        }
+        const CellState sa = velocity(moments_of(fa), p), sb = velocity(moments_of(fb), p);
+        c.rho = make_float2(sa.rho, sb.rho);
+        c.ux = make_float2(sa.ux, sb.ux);
+        c.uy = make_float2(sa.uy, sb.uy);
+        c.uz = make_float2(sa.uz, sb.uz);
+        wall_node(fa, oa, ca0, p, y == 0, 0xffffffffu, twx.x, twz.x);
+        wall_node(fb, ob, ca1, p, y == 0, 0xffffffffu, twx.y, twz.y);
+#pragma unroll
+        for (int a = 0; a < Q; ++a) f[a] = make_float2(oa[a], ob[a]);
+        if (valid) {
+            float4 *t = reinterpret_cast<float4 *>(
+                reinterpret_cast<float2 *>(tw_out) + ((long long)((y == 0 ? 0 : 1) * g.nz + z) * g.nx + x0));
+            *t = make_float4(twx.x, twz.x, twx.y, twz.y);
+        }
+    } else {
+        c = collide_pair<COLL>(f, p, row_smag(p, y, g.ny));
+    }
+
+    if (!node_row && (y == 0 || y == g.ny - 1)) {
         // the wall layer of both cells, lane by lane (all 32 lanes are present)
         float fa[Q], fb[Q];
 #pragma unroll

@@ -102,7 +102,7 @@ __device__ __forceinline__ void issue_row(const T *__restrict__ src, const Geom 
     const bool crosses = (y == 0 && ey == 1) || (y == g.ny - 1 && ey == -1);
     if (crosses) {
         ys = y;
-        if (wall == WALL_BB) {
+        if (bb_map(wall)) {
             slot = opp_of(a);
             zs = z;
         } else {
@@ -122,7 +122,7 @@ __device__ __forceinline__ void read_rows(const T *stage, int nx, int wall, int 
     for (int a = 0; a < Q; ++a) {
         const T *b = stage + (long long)a * nx;
         const int ex = ex_of(a), ey = ey_of(a);
-        const bool bb_cross = wall == WALL_BB && ((bottom && ey == 1) || (top && ey == -1));
+        const bool bb_cross = bb_map(wall) && ((bottom && ey == 1) || (top && ey == -1));
         if (ex == 0 || bb_cross) {
             f[a] = lds2<T>(b + x0);
         } else if (ex == 1) {   // cells read x - 1

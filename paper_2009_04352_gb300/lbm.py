@@ -27,7 +27,7 @@ LBM_ERR_OOM = -3
 LBM_ERR_DIVERGED = -4
 LBM_ERR_STATE = -5
 
-WALL_BB, WALL_WFB, WALL_FREESLIP = 0, 1, 2
+WALL_BB, WALL_WFB, WALL_FREESLIP, WALL_WFB_NODE = 0, 1, 2, 3
 KERNEL_AUTO, KERNEL_CELL, KERNEL_PAIR, KERNEL_TMA, KERNEL_QUAD = 0, 1, 2, 3, 4
 COLLISION_BGK, COLLISION_MRT = 0, 1
 LAW_SPALDING, LAW_LOG, LAW_POWER = 0, 1, 2

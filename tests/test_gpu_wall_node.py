@@ -1,0 +1,141 @@
+"""The full-way (wall-node) WFB on the GPU against the oracle: the one-cell and
+two-cell kernels, FP32 and FP16 storage, ragged grids down to one fluid layer,
+the batch, and the kernel forms and layouts that have no wall-node form."""
+import functools
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2009_04352_gb300 import lbm, workload
+
+pytestmark = pytest.mark.gpu
+
+TOL = {lbm.FP32: 1e-5, lbm.FP16_SHIFTED: 5e-3}
+TOL_RHO = {lbm.FP32: 3e-4, lbm.FP16_SHIFTED: 5e-2}
+# the parity configuration (tau0 0.52, C_s 0.1) on wall nodes: 64 x 33 x 32,
+# D = 16 between the wall nodes as in the 64 x 32 x 32 halfway case
+NODE_C1 = workload.CASES["c1"].with_(name="c1 on wall nodes 64x33x32", ny=33, wall=workload.WALL_WFB_NODE)
+# first fluid node at y+ = 40 (the log region of the wall laws), tau0 = 0.50014
+NODE = workload.derive_channel("wall-node channel 64x33x32", 64, 33, 32, 640.0,
+                               wall=workload.WALL_WFB_NODE, seed=23)
+RAGGED = [NODE.with_(nx=37, ny=6, nz=5), NODE.with_(nx=2, ny=3, nz=3), NODE.with_(nx=34, ny=4, nz=3),
+          NODE.with_(nx=130, ny=5, nz=2)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2009_04352_gb300 import build
+    build.build()
+    oracle.build()
+
+
+def rel(a, b):
+    return float(np.max(np.abs(np.asarray(a, dtype=np.float64) - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_run(case, steps, law=0):
+    L = oracle.Lattice.from_case(case)
+    L.set_wall_law(law)
+    L.init_channel(workload.u_mean_profile(case), workload.noise_amplitude(case), case.seed)
+    L.step(steps)
+    rho, u = L.moments()
+    out = dict(rho=rho, u=u, tw=L.wall_stress(), f=L.populations())
+    L.close()
+    return out
+
+
+def _channel(case, precision, kernel):
+    ch = lbm.Channel.from_case(case, precision=precision)
+    ch.set_kernel(kernel)
+    ch.init_channel(workload.u_mean_profile(case), workload.noise_amplitude(case), case.seed)
+    return ch
+
+
+@pytest.mark.parametrize("kernel", [lbm.KERNEL_PAIR, lbm.KERNEL_CELL])
+@pytest.mark.parametrize("precision", [lbm.FP32, lbm.FP16_SHIFTED])
+def test_wall_node_parity_100_steps(precision, kernel):
+    ref = oracle_run(NODE_C1, 100)
+    ch = _channel(NODE_C1, precision, kernel)
+    assert ch.kernel == kernel
+    ch.step(100)
+    rho, u = ch.moments()
+    assert rel(u, ref["u"]) <= TOL[precision]
+    assert rel(rho - 1.0, ref["rho"] - 1.0) <= TOL_RHO[precision]
+    w = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)[:, None, None, None]
+    assert rel(ch.populations() - w, ref["f"] - w) <= TOL[precision]
+    assert rel(ch.wall_stress(), ref["tw"]) <= 10 * TOL[precision]
+    ch.close()
+
+
+@pytest.mark.parametrize("kernel", [lbm.KERNEL_PAIR, lbm.KERNEL_CELL])
+@pytest.mark.parametrize("precision", [lbm.FP32, lbm.FP16_SHIFTED])
+def test_wall_node_log_region_100_steps(precision, kernel):
+    """Wall law in its log region (R ~ 500) at tau0 near 1/2: velocity and
+    wall stress (the populations of a weakly damped FP16 run drift a little
+    past the parity configuration's bound, the moments do not)."""
+    ref = oracle_run(NODE, 100)
+    ch = _channel(NODE, precision, kernel)
+    ch.step(100)
+    _, u = ch.moments()
+    assert rel(u, ref["u"]) <= TOL[precision]
+    assert rel(ch.wall_stress(), ref["tw"]) <= 10 * TOL[precision]
+    ch.close()
+
+
+@pytest.mark.parametrize("case", RAGGED, ids=lambda c: f"{c.nx}x{c.ny}x{c.nz}")
+def test_wall_node_ragged(case):
+    ref = oracle_run(case, 40)
+    for kernel in ([lbm.KERNEL_PAIR, lbm.KERNEL_CELL] if case.nx % 2 == 0 else [lbm.KERNEL_CELL]):
+        ch = _channel(case, lbm.FP32, kernel)
+        ch.step(40)
+        _, u = ch.moments()
+        assert rel(u, ref["u"]) <= TOL[lbm.FP32], kernel
+        assert rel(ch.wall_stress(), ref["tw"]) <= 10 * TOL[lbm.FP32], kernel
+        ch.close()
+
+
+def test_wall_node_log_law_and_mass():
+    case = NODE.with_(wall_law=lbm.LAW_LOG)
+    ref = oracle_run(case, 60, law=1)
+    ch = _channel(case, lbm.FP32, lbm.KERNEL_PAIR)
+    m0 = ch.conservation()[0]
+    ch.step(60)
+    _, u = ch.moments()
+    assert rel(u, ref["u"]) <= TOL[lbm.FP32]
+    assert rel(ch.wall_stress(), ref["tw"]) <= 10 * TOL[lbm.FP32]
+    assert abs(ch.conservation()[0] - m0) <= 1e-6 * m0
+    ch.close()
+
+
+@pytest.mark.parametrize("precision", [lbm.FP32, lbm.FP16_SHIFTED])
+def test_wall_node_batch_member_equals_channel(precision):
+    members = [NODE.with_(seed=41), NODE.with_(nx=66, ny=9, nz=4, seed=42, wall=workload.WALL_WFB)]
+    b = lbm.Batch(members, precision=precision)
+    for m, c in zip(b.members, members):
+        m.init_channel(workload.u_mean_profile(c), workload.noise_amplitude(c), c.seed)
+    b.step(25)
+    for i, c in enumerate(members):
+        ch = _channel(c, precision, lbm.KERNEL_PAIR)
+        ch.step(25)
+        assert np.array_equal(b.members[i].populations(), ch.populations()), i
+        assert np.array_equal(b.members[i].wall_stress(), ch.wall_stress()), i
+        ch.close()
+    b.close()
+
+
+def test_wall_node_rejects_other_forms():
+    ch = lbm.Channel.from_case(NODE, precision=lbm.FP16_SHIFTED)
+    assert ch.kernel == lbm.KERNEL_PAIR          # AUTO does not pick the four-cell form
+    for k in (lbm.KERNEL_QUAD, lbm.KERNEL_TMA):
+        with pytest.raises(lbm.LbmError):
+            ch.set_kernel(k)
+    ch.close()
+    with pytest.raises(lbm.LbmError):
+        lbm.Channel.from_case(NODE, layout=lbm.AA)
+    with pytest.raises(lbm.LbmError):
+        lbm.Channel.from_case(NODE.with_(ny=2))
