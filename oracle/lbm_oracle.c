@@ -199,23 +199,25 @@ void or_mrt_matrix(double *M)
 }
 
 /* Relaxation rates of the D3Q19 MRT model after d'Humieres et al. (2002):
- * s_e = 1.19, s_eps = 1.4, s_q = 1.2, s_m = 1.98; the five stress moments
- * (9, 11, 13, 14, 15) and the two pi moments (10, 12) relax with 1/tau_eff
- * (the published s_pi = 1.4 is replaced, see below); the conserved moments
- * (0, 3, 5, 7) take 1 (their value does not enter the result). */
+ * s_e = 1.19, s_eps = 1.4, s_m = 1.98; the five stress moments
+ * (9, 11, 13, 14, 15) and the two pi moments (10, 12) relax with 1/tau_eff,
+ * and the energy fluxes q with 1.99 (the published s_pi = 1.4 and s_q = 1.2
+ * are replaced, see below); the conserved moments (0, 3, 5, 7) take 1 (their
+ * value does not enter the result). */
 void or_mrt_rates(double tau, double *s)
 {
     for (int i = 0; i < Q; ++i) s[i] = 1.0;
     s[1] = 1.19;
     s[2] = 1.4;
-    s[4] = s[6] = s[8] = 1.2;
     s[16] = s[17] = s[18] = 1.98;
     s[9] = s[11] = s[13] = s[14] = s[15] = 1.0 / tau;
-    /* the fourth-order pi moments relax with the shear rate too: with the
-     * published 1.4 the scheme is linearly unstable for tau0 below about 0.502
-     * (a normal-stress mode grows at wavenumbers near 2 pi / 3), which is
-     * where the channel runs of Sec. 3.1 operate (tau0 ~ 0.5002) */
+    /* The channel runs of Sec. 3.1 operate at tau0 ~ 0.5002, where the
+     * published rates make the scheme linearly unstable: a normal-stress mode
+     * grows at rest unless the fourth-order pi moments relax with the shear
+     * rate, and with a mean flow of a few percent of the lattice speed unless
+     * the energy fluxes q relax near 2 as well. */
     s[10] = s[12] = 1.0 / tau;
+    s[4] = s[6] = s[8] = 1.99;
 }
 
 /* One MRT collision with the same moments, equilibrium, Smagorinsky closure

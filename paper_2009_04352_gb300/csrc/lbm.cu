@@ -461,7 +461,7 @@ int lbm_create_handle(lbm_grid g, double tau, double C_s, const double force[3],
         double r = 1.0;
         if (i == 1) r = 1.19;
         if (i == 2) r = 1.4;   // rows 10 and 12 relax with 1/tau_eff (mrt_stress)
-        if (i == 4 || i == 6 || i == 8) r = 1.2;
+        if (i == 4 || i == 6 || i == 8) r = 1.99;   // q: linear stability near tau0 = 1/2
         if (i >= 16) r = 1.98;
         h->p.mrt_s[i] = (float)r;
         double gc = 0.0, gu[3] = {0.0, 0.0, 0.0};

@@ -151,7 +151,7 @@ __host__ __device__ constexpr int mrt_norm(int i)
 // Rows relaxing with 1/tau_eff: the five stress moments and the two
 // fourth-order pi moments (10, 12). With the published pi rate of 1.4 the
 // scheme is linearly unstable for tau0 below about 0.502, where the channel
-// runs operate.
+// runs operate (the host also sets the q rates to 1.99 for the same reason).
 __host__ __device__ constexpr bool mrt_stress(int i)
 {
     return i == 9 || i == 10 || i == 11 || i == 12 || i == 13 || i == 14 || i == 15;

@@ -79,7 +79,10 @@ def run(case: workload.ChannelCase, t_spin: float, t_end: float, samples_per_t: 
     ch.sync()
     wall_s = time.perf_counter() - t0
     stats, wstats, ns = ch.plane_stats()
-    cons = ch.conservation()
+    try:
+        cons = ch.conservation()
+    except lbm.LbmError:          # a run that diverged reports non-finite sums
+        cons = np.array([np.nan])
     ch.close()
     return summarise(case, stats, wstats, ns, np.stack(taus), dict(
         steps=n_end, spin_up_steps=n_spin, sample_every=every, samples=int(ns), T_steps=T,

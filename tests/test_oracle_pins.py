@@ -447,8 +447,8 @@ def test_mrt_conserves_mass_and_adds_force(oracle_lib, seed):
     # moments with 1 / tau_eff
     M = oracle_lib.mrt_matrix()
     s = oracle_lib.mrt_rates(tau)
-    assert s[1] == 1.19 and s[2] == 1.4 and s[4] == 1.2 and s[16] == 1.98 and s[9] == 1.0 / tau
-    assert s[10] == s[12] == 1.0 / tau
+    assert s[1] == 1.19 and s[2] == 1.4 and s[16] == 1.98 and s[9] == 1.0 / tau
+    assert s[10] == s[12] == 1.0 / tau and s[4] == s[6] == s[8] == 1.99
 
 
 def _shear_wave_decay(oracle_lib, collision, tau, nz=64, steps=400, amp=1e-3):
@@ -754,32 +754,42 @@ def test_wall_node_rest_state_and_ny3(oracle_lib):
     assert abs(math.fsum(L.populations().ravel()) - m0) <= 1e-12 * m0
 
 
-def _max_amplification(oracle_lib, rates, nk=9):
-    """Largest |eigenvalue| of one linearised step (collision about rest, then
-    streaming) over plane waves exp(i k . x), k on a grid of [0, pi]^3 (von
-    Neumann analysis of the scheme)."""
+def _max_amplification(oracle_lib, rates, nk=9, U=0.0):
+    """Largest |eigenvalue| of one linearised step (collision about rho = 1,
+    u = (U, 0, 0), then streaming) over plane waves exp(i k . x), k on a grid
+    of [-pi, pi] x [0, pi]^2 (von Neumann analysis of the scheme)."""
     e, w, _, _ = oracle_lib.table()
     e = np.asarray(e, dtype=float)
     w = np.asarray(w, dtype=float)
     M = np.asarray(oracle_lib.mrt_matrix(), dtype=float).reshape(19, 19)
     Minv = M.T / np.sum(M * M, axis=1)[None, :]
-    E = w[:, None] * (1 + 3 * e @ e.T)     # d f^eq / d f at rest
+    u = np.array([U, 0.0, 0.0])
+    eu = e @ u
+    feq = w * (1 + 3 * eu + 4.5 * eu * eu - 1.5 * u @ u)
+    dfeq_du = w[:, None] * (3 * e + 9 * eu[:, None] * e - 3 * u[None, :])
+    # d f^eq_a / d f_b with rho = sum f, u = sum e f / rho
+    E = feq[:, None] + dfeq_du @ (e - u[None, :]).T
     C = np.eye(19) - Minv @ np.diag(rates) @ M @ (np.eye(19) - E)
     g = np.linspace(0, math.pi, nk)
-    ks = np.array([[a, b, c] for a in g for b in g for c in g[::2]])
+    ks = np.array([[a, b, c] for a in np.linspace(-math.pi, math.pi, nk) for b in g for c in g[::2]])
     A = np.exp(-1j * ks @ e.T)[:, :, None] * C[None]
     return float(np.max(np.abs(np.linalg.eigvals(A))))
 
 
 def test_mrt_linearly_stable_near_half(oracle_lib):
-    """Von Neumann analysis at the channel runs' tau0 (0.5002) and closer to
-    1/2: the oracle's MRT rates amplify no plane wave (|lambda| <= 1, like BGK),
-    while the published rate set with s_pi = 1.4 does (|lambda| ~ 1.007), the
-    reason the pi moments relax with 1 / tau_eff here."""
-    for tau in (0.5002, 0.50005, 0.52, 0.8):
+    """Von Neumann analysis at the channel runs' tau0 (0.5002 .. 0.5004) and
+    further from 1/2, at rest and with a mean flow of 0.05: the oracle's MRT
+    rates amplify no plane wave (|lambda| <= 1, like BGK). The published rate
+    set does (s_pi = 1.4: |lambda| ~ 1.007 at rest; s_q = 1.2: ~ 1.001 with
+    the flow), the reason those rates are replaced."""
+    for tau in (0.5002, 0.50035, 0.52, 0.8):
         s = np.asarray(oracle_lib.mrt_rates(tau), dtype=float)
-        assert _max_amplification(oracle_lib, s) <= 1.0 + 1e-9, tau
-        assert _max_amplification(oracle_lib, np.full(19, 1.0 / tau)) <= 1.0 + 1e-9
+        for U in (0.0, 0.05):
+            assert _max_amplification(oracle_lib, s, U=U) <= 1.0 + 1e-9, (tau, U)
+            assert _max_amplification(oracle_lib, np.full(19, 1.0 / tau), U=U) <= 1.0 + 1e-9
     s = np.asarray(oracle_lib.mrt_rates(0.5002), dtype=float)
     s[10] = s[12] = 1.4
     assert _max_amplification(oracle_lib, s) > 1.005
+    s = np.asarray(oracle_lib.mrt_rates(0.50035), dtype=float)
+    s[4] = s[6] = s[8] = 1.2
+    assert _max_amplification(oracle_lib, s, U=0.05) > 1.0005
