@@ -37,7 +37,7 @@ NOMINAL_HBM_GBS = 7900.0      # GB300 HBM3e nominal, for the second fraction
 # dominant kernel from one ncu capture of the current kernel build, keyed by
 # (workload, storage, layout); the captures are summarised under profiles/.
 # Absent keys report null.
-NCU_TRAFFIC = {("c2", "fp32", "pull"): 264.4e6,
+NCU_TRAFFIC = {("c2", "fp32", "pull"): 264.6e6,
                # mean of the even and the odd AA step launch
                ("c3", "fp16", "aa"): 1280.0e6}
 
