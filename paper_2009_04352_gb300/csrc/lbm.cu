@@ -268,10 +268,29 @@ int launch_step_c(lbm_handle *h, cudaStream_t s, int src, bool stats)
                 launch_rows_t<float, 4, COLL>(h, s, src, stats);
         }
     } else if (h->kernel == LBM_KERNEL_QUAD) {
+        // BGK: interior rows, then the two wall rows (the wall layer lives only
+        // in the second instantiation); MRT: one launch over every row (its
+        // interior-only instantiation spills more than the combined one)
         const __half *ah = (const __half *)a;
         __half *bh = (__half *)b;
-        e = stats ? launch_pdl(lbm::k_step_quad<true, COLL>, grid, block, 0, s, ah, bh, h->g, h->p, h->tw, h->part)
-                  : launch_pdl(lbm::k_step_quad<false, COLL>, grid, block, 0, s, ah, bh, h->g, h->p, h->tw, h->part);
+        if (COLL != lbm::COLL_BGK) {
+            e = stats ? launch_pdl(lbm::k_step_quad<true, COLL, lbm::ROWS_ALL>, grid, block, 0, s, ah, bh, h->g,
+                                   h->p, h->tw, h->part)
+                      : launch_pdl(lbm::k_step_quad<false, COLL, lbm::ROWS_ALL>, grid, block, 0, s, ah, bh, h->g,
+                                   h->p, h->tw, h->part);
+        } else if (h->g.ny > 2) {
+            const dim3 gi(grid.x, h->g.ny - 2, grid.z);
+            e = stats ? launch_pdl(lbm::k_step_quad<true, COLL, lbm::ROWS_INTERIOR>, gi, block, 0, s, ah, bh, h->g,
+                                   h->p, h->tw, h->part)
+                      : launch_pdl(lbm::k_step_quad<false, COLL, lbm::ROWS_INTERIOR>, gi, block, 0, s, ah, bh, h->g,
+                                   h->p, h->tw, h->part);
+        }
+        const dim3 gw(grid.x, 2, grid.z);
+        if (COLL == lbm::COLL_BGK && e == cudaSuccess)
+            e = stats ? launch_pdl(lbm::k_step_quad<true, COLL, lbm::ROWS_WALL>, gw, block, 0, s, ah, bh, h->g, h->p,
+                                   h->tw, h->part)
+                      : launch_pdl(lbm::k_step_quad<false, COLL, lbm::ROWS_WALL>, gw, block, 0, s, ah, bh, h->g, h->p,
+                                   h->tw, h->part);
     } else if (h->kernel == LBM_KERNEL_PAIR) {
         if (half) {
             const __half *ah = (const __half *)a;

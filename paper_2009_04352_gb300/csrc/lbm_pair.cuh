@@ -183,6 +183,38 @@ struct PairState {
     float2 rho, ux, uy, uz;
 };
 
+// wall_layer() of lbm_kernels.cuh for a packed pair of first-layer cells:
+// the wall stress lane by lane, the correction of the four wall-bound
+// populations with packed adds (the same single roundings as the scalar form).
+__device__ __forceinline__ void wall_layer_pair(float2 (&f)[Q], const PairState &c, const Phys &p, bool bottom,
+                                                float2 &twx, float2 &twz)
+{
+    twx = make_float2(0.f, 0.f);
+    twz = make_float2(0.f, 0.f);
+    if (p.wall == WALL_WFB) {
+        const CellState ca{c.rho.x, c.ux.x, c.uy.x, c.uz.x}, cb{c.rho.y, c.ux.y, c.uy.y, c.uz.y};
+        wfb_stress(ca, p, 0xffffffffu, twx.x, twz.x);
+        wfb_stress(cb, p, 0xffffffffu, twx.y, twz.y);
+        const float2 hx = make_float2(0.5f * twx.x, 0.5f * twx.y), hz = make_float2(0.5f * twz.x, 0.5f * twz.y);
+        const float2 mhx = make_float2(-hx.x, -hx.y), mhz = make_float2(-hz.x, -hz.y);
+        if (bottom) {
+            f[13] = __fadd2_rn(f[13], hx);
+            f[8] = __fadd2_rn(f[8], mhx);
+            f[18] = __fadd2_rn(f[18], hz);
+            f[12] = __fadd2_rn(f[12], mhz);
+        } else {
+            f[7] = __fadd2_rn(f[7], hx);
+            f[14] = __fadd2_rn(f[14], mhx);
+            f[11] = __fadd2_rn(f[11], hz);
+            f[17] = __fadd2_rn(f[17], mhz);
+        }
+    } else if (p.wall == WALL_BB) {
+        const int a = bottom ? 13 : 7, b = bottom ? 8 : 14, cz = bottom ? 18 : 11, dz = bottom ? 12 : 17;
+        twx = make_float2(-2.f * (f[a].x - f[b].x), -2.f * (f[a].y - f[b].y));
+        twz = make_float2(-2.f * (f[cz].x - f[dz].x), -2.f * (f[cz].y - f[dz].y));
+    }
+}
+
 // collide() of lbm_kernels.cuh for two cells (in place: f becomes f*),
 // organised around the opposite pairs k = 0..8 (directions 2k+1, 2k+2):
 // s_k = f_a + f_b and d_k = f_a - f_b carry all moments the update needs,

@@ -192,17 +192,7 @@ __device__ __forceinline__ void quad_half(uint2 (&r)[Q], const Phys &p, float sm
     const PairState c = collide_pair<COLL>(f, p, smag);
     float2 twx = bc(0.f), twz = bc(0.f);
     if (wall_row) {
-        float fa[Q], fb[Q];
-#pragma unroll
-        for (int a = 0; a < Q; ++a) {
-            fa[a] = f[a].x;
-            fb[a] = f[a].y;
-        }
-        const CellState ca{c.rho.x, c.ux.x, c.uy.x, c.uz.x}, cb{c.rho.y, c.ux.y, c.uy.y, c.uz.y};
-        wall_layer(fa, ca, p, bottom, 0xffffffffu, twx.x, twz.x);
-        wall_layer(fb, cb, p, bottom, 0xffffffffu, twx.y, twz.y);
-#pragma unroll
-        for (int a = 0; a < Q; ++a) f[a] = make_float2(fa[a], fb[a]);
+        wall_layer_pair(f, c, p, bottom, twx, twz);
         tw = make_float4(twx.x, twz.x, twx.y, twz.y);
     }
 #pragma unroll
@@ -228,7 +218,12 @@ __device__ __forceinline__ void quad_half(uint2 (&r)[Q], const Phys &p, float sm
 // One tile: the x-quads xb * blockDim.x + threadIdx.x of row (y, z), i.e.
 // cells [4 xb blockDim.x, 4 (xb + 1) blockDim.x). With STATS the block writes
 // its FP64 partial sums to part_blk[0..K_PART).
-template <bool STATS, int COLL = COLL_BGK, int LAY = LAY_PULL>
+// Row sets of the two-lattice four-cell step: every row, the interior rows
+// 1 .. ny - 2 only (their instantiation carries no wall-layer code), or the
+// two wall rows only.
+enum { ROWS_ALL = 0, ROWS_INTERIOR = 1, ROWS_WALL = 2 };
+
+template <bool STATS, int COLL = COLL_BGK, int LAY = LAY_PULL, int ROWS = ROWS_ALL>
 __device__ __forceinline__ void quad_tile(const __half *src, __half *dst, const Geom &g, const Phys &p,
                                           float *__restrict__ tw_out, double *__restrict__ part_blk, int xb, int y,
                                           int z)
@@ -240,14 +235,14 @@ __device__ __forceinline__ void quad_tile(const __half *src, __half *dst, const 
     const int zm = z == 0 ? g.nz - 1 : z - 1, zp = z == g.nz - 1 ? 0 : z + 1;
 
     uint2 r[Q];
-    if (y == 0)
+    if (ROWS != ROWS_INTERIOR && y == 0)
         gather_quad<ROW_BOTTOM, LAY>(src, g, p.wall, xl, y, z, zm, zp, lane, r);
-    else if (y == g.ny - 1)
+    else if (ROWS != ROWS_INTERIOR && y == g.ny - 1)
         gather_quad<ROW_TOP, LAY>(src, g, p.wall, xl, y, z, zm, zp, lane, r);
     else
         gather_quad<ROW_INTERIOR, LAY>(src, g, p.wall, xl, y, z, zm, zp, lane, r);
 
-    const bool wall_row = y == 0 || y == g.ny - 1;
+    const bool wall_row = ROWS == ROWS_INTERIOR ? false : (ROWS == ROWS_WALL ? true : (y == 0 || y == g.ny - 1));
     double v[K_PART];
     if (STATS) {
 #pragma unroll
@@ -279,16 +274,23 @@ __device__ __forceinline__ void quad_tile(const __half *src, __half *dst, const 
     if (STATS) block_reduce_store<K_PART>(v, part_blk);
 }
 
-template <bool STATS, int COLL = COLL_BGK>
+// The two-lattice step over the row set ROWS: grid.y is ny (ROWS_ALL), ny - 2
+// (ROWS_INTERIOR, row blockIdx.y + 1) or 2 (ROWS_WALL, rows 0 and ny - 1).
+// The step runs as an interior launch and a wall-row launch, so that the wall
+// layer's code does not shape the register allocation of the interior rows.
+template <bool STATS, int COLL = COLL_BGK, int ROWS = ROWS_ALL>
 __global__ void __launch_bounds__(128, LBM_QUAD_MIN_BLOCKS) k_step_quad(const __half *__restrict__ src,
                                                                          __half *__restrict__ dst, Geom g, Phys p,
                                                                          float *__restrict__ tw_out,
                                                                          double *__restrict__ part)
 {
     pdl_begin();
-    const int y = blockIdx.y, z = blockIdx.z;
+    const int y = ROWS == ROWS_INTERIOR ? (int)blockIdx.y + 1
+                                        : (ROWS == ROWS_WALL ? (blockIdx.y == 0 ? 0 : g.ny - 1) : (int)blockIdx.y);
+    const int z = blockIdx.z;
     const long long blk = ((long long)y * g.nz + z) * gridDim.x + blockIdx.x;
-    quad_tile<STATS, COLL>(src, dst, g, p, tw_out, STATS ? part + blk * K_PART : nullptr, blockIdx.x, y, z);
+    quad_tile<STATS, COLL, LAY_PULL, ROWS>(src, dst, g, p, tw_out, STATS ? part + blk * K_PART : nullptr,
+                                           blockIdx.x, y, z);
 }
 
 // The four-cell step on the single AA array (LAY_AA_EVEN or LAY_AA_ODD).
