@@ -444,7 +444,11 @@ __device__ __forceinline__ PairState collide_pair(float2 (&f)[Q], const Phys &p,
 //
 // LAY selects the storage scheme (LAY_PULL: src and dst are the two lattices;
 // LAY_AA_EVEN / LAY_AA_ODD: src == dst, the single AA array).
-template <typename T, bool STATS, int COLL = COLL_BGK, int LAY = LAY_PULL>
+// Row sets a tile instantiation serves: any row, the interior rows only (no
+// wall-layer code in the instantiation), or the two wall rows only.
+enum { ROWS_ALL = 0, ROWS_INTERIOR = 1, ROWS_WALL = 2 };
+
+template <typename T, bool STATS, int COLL = COLL_BGK, int LAY = LAY_PULL, int ROWS = ROWS_ALL>
 __device__ __forceinline__ void pair_tile(const T *src, T *dst, const Geom &g, const Phys &p,
                                           float *__restrict__ tw_out, double *__restrict__ part_blk, int xb, int y,
                                           int z)
@@ -458,7 +462,8 @@ __device__ __forceinline__ void pair_tile(const T *src, T *dst, const Geom &g, c
     // wall node of the full-way WFB (two-lattice layout only): no collision;
     // tau_w from the first fluid node, whose state is gathered first so that
     // its populations are dead before the node's own are loaded
-    const bool node_row = LAY == LAY_PULL && p.wall == WALL_NODE && (y == 0 || y == g.ny - 1);
+    const bool node_row =
+        ROWS != ROWS_INTERIOR && LAY == LAY_PULL && p.wall == WALL_NODE && (y == 0 || y == g.ny - 1);
     CellState ca0{}, ca1{};
     if (node_row) {
         float2 fa[Q];
@@ -474,9 +479,9 @@ __device__ __forceinline__ void pair_tile(const T *src, T *dst, const Geom &g, c
     }
 
     float2 f[Q];
-    if (y == 0)
+    if (ROWS != ROWS_INTERIOR && y == 0)
         gather_pair<T, ROW_BOTTOM, LAY>(src, g, p.wall, xl, y, z, zm, zp, lane, f);
-    else if (y == g.ny - 1)
+    else if (ROWS != ROWS_INTERIOR && y == g.ny - 1)
         gather_pair<T, ROW_TOP, LAY>(src, g, p.wall, xl, y, z, zm, zp, lane, f);
     else
         gather_pair<T, ROW_INTERIOR, LAY>(src, g, p.wall, xl, y, z, zm, zp, lane, f);
@@ -508,7 +513,7 @@ __device__ __forceinline__ void pair_tile(const T *src, T *dst, const Geom &g, c
         c = collide_pair<COLL>(f, p, row_smag(p, y, g.ny));
     }
 
-    if (!node_row && (y == 0 || y == g.ny - 1)) {
+    if (ROWS != ROWS_INTERIOR && !node_row && (y == 0 || y == g.ny - 1)) {
         // the wall layer of both cells, lane by lane (all 32 lanes are present)
         float fa[Q], fb[Q];
 #pragma unroll

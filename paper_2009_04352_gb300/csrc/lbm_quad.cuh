@@ -218,10 +218,9 @@ __device__ __forceinline__ void quad_half(uint2 (&r)[Q], const Phys &p, float sm
 // One tile: the x-quads xb * blockDim.x + threadIdx.x of row (y, z), i.e.
 // cells [4 xb blockDim.x, 4 (xb + 1) blockDim.x). With STATS the block writes
 // its FP64 partial sums to part_blk[0..K_PART).
-// Row sets of the two-lattice four-cell step: every row, the interior rows
-// 1 .. ny - 2 only (their instantiation carries no wall-layer code), or the
-// two wall rows only.
-enum { ROWS_ALL = 0, ROWS_INTERIOR = 1, ROWS_WALL = 2 };
+// The two-lattice four-cell step serves the row sets of pair_tile (lbm_pair.cuh):
+// every row, the interior rows 1 .. ny - 2 only (their instantiation carries
+// no wall-layer code), or the two wall rows only.
 
 template <bool STATS, int COLL = COLL_BGK, int LAY = LAY_PULL, int ROWS = ROWS_ALL>
 __device__ __forceinline__ void quad_tile(const __half *src, __half *dst, const Geom &g, const Phys &p,
