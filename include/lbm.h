@@ -139,7 +139,9 @@ typedef enum {
  *         shared-memory ring with bulk asynchronous copies (full/empty
  *         mbarriers, 2-4 stages); nx a multiple of 64 whose rows fit the ring.
  *   QUAD: four cells per thread, 8-byte loads and stores; FP16 storage and nx a
- *         multiple of 4.
+ *         multiple of 4 (halfway walls). With the two-lattice layout and BGK
+ *         a step is two launches, the interior rows and then the two wall
+ *         rows.
  *   AUTO: QUAD where allowed, else PAIR for even nx, else CELL. */
 typedef enum {
     LBM_KERNEL_AUTO = 0,

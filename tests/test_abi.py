@@ -102,3 +102,19 @@ def test_create_from_buffers_rejects_bad_buffers_without_device():
             lbm.lbm_create_from_buffers(8, 8, 8, 0.6, 0.1, (1e-6, 0, 0), kw["pop0"], kw["pop1"],
                                         layout=kw["layout"], stream=0)
         assert ei.value.code == lbm.LBM_ERR_ARG
+
+
+def test_bench_launch_and_kernel_bookkeeping():
+    """bench.py's count of step-kernel launches and its name of the selected
+    kernel follow the library's selection rules (host logic only)."""
+    import bench
+    from paper_2009_04352_gb300 import lbm, workload
+    c2, c3 = workload.CASES["c2"], workload.CASES["c3"]
+    assert bench.launches_per_step(c2, lbm.FP32) == 1
+    assert bench.launches_per_step(c3, lbm.FP16_SHIFTED) == 2           # interior + wall rows
+    assert bench.launches_per_step(c3, lbm.FP16_SHIFTED, lbm.AA) == 1
+    assert bench.launches_per_step(c3.with_(ny=2), lbm.FP16_SHIFTED) == 1
+    assert bench.headline_kernel(c2, lbm.FP32) == "k_step_pair"
+    assert bench.headline_kernel(c3, lbm.FP16_SHIFTED) == "k_step_quad"
+    assert bench.headline_kernel(c3, lbm.FP16_SHIFTED, lbm.AA) == "k_step_quad_aa"
+    assert bench.headline_kernel(c2.with_(nx=37), lbm.FP32) == "k_step"
