@@ -6,8 +6,10 @@ CPU-baseline leg may import this module; the library under
 
 Every function here is a thin ctypes call into ``lbm_oracle.c``; the arithmetic
 lives there, written in plain double precision as the paper's equations read
-(Eqs. 1-2 and 14-17, Sec. 2-3), with the readings of the silent or garbled
-passages listed in the design notes.
+(Eqs. 1-2 and 14-17, Sec. 2-3). Where the paper is silent or garbled (the
+corrected populations of Eq. 14c, the wall distance of Eq. 17, the forcing
+scheme, the Smagorinsky closure) the function concerned states the reading it
+takes in its comment.
 
 Parity status: every oracle function has at least one independent pin in
 ``tests/test_oracle_pins.py``; none is marked "parity unpinned".
