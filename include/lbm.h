@@ -97,8 +97,9 @@ typedef enum {
  * is the wall distance entering y+ = y1 u_tau / nu (Eq. 17); 1.0 reproduces
  * the first-layer y+ printed in Table 1. nu is the molecular viscosity used by
  * the wall law; a value <= 0 selects (tau - 1/2) / 3. newton_iters caps the
- * Newton iterations per wall cell and step (<= 0 selects 12); iteration stops
- * earlier once every lane of a warp has a relative step below 1e-7. law is an
+ * Newton iterations per wall cell and step (<= 0 selects 12); each cell keeps
+ * its value from its first relative step below 1e-7 on (the result does not
+ * depend on the kernel form). law is an
  * lbm_wall_law (0, the zero-initialised default, is Spalding's law); another
  * value, or a log law whose two branches never cross (B <= (1 + ln kappa) /
  * kappa), makes lbm_create / lbm_batch_create fail with LBM_ERR_ARG. */
@@ -141,7 +142,7 @@ typedef enum {
  *   QUAD: four cells per thread, 8-byte loads and stores; FP16 storage and nx a
  *         multiple of 4 (halfway walls). With the two-lattice layout and BGK
  *         a step is two launches, the interior rows and then the two wall
- *         rows.
+ *         rows, the latter with the two-cell tile (the same bits).
  *   AUTO: QUAD where allowed, else PAIR for even nx, else CELL. */
 typedef enum {
     LBM_KERNEL_AUTO = 0,
@@ -214,7 +215,11 @@ int lbm_set_stats_every(lbm_handle *h, int every);
 
 /* Advance n >= 0 time steps (Eq. 1 with the wall treatment of Eqs. 14-17).
  * Asynchronous on the handle's stream; steps without sampling are replayed
- * from CUDA graphs. */
+ * from CUDA graphs of 16 steps. The first call with n > 0 after lbm_create,
+ * lbm_set_kernel, lbm_set_les or lbm_set_wait_limit captures, instantiates and
+ * uploads both of those graphs (one per start phase), whatever n is, so a
+ * short warm-up call leaves nothing to build inside a later timed run; make
+ * that first call outside any stream capture of the caller's own. */
 int lbm_step(lbm_handle *h, int n);
 
 /* Number of steps taken since the last (re)initialisation. */
@@ -235,8 +240,11 @@ typedef enum {
 
 /* LES model (Sec. 3.1). collision: BGK, or the D3Q19 MRT of d'Humieres et al.
  * (2002) (moments rho, e, eps, j, q, 3p_xx, 3pi_xx, p_ww, pi_ww, p_xy, p_yz,
- * p_xz, m; ghost rates 1.19, 1.4, 1.2, 1.4, 1.98; the five stress moments relax
- * with 1/tau_eff; equilibrium moments M f^eq; Guo forcing in moment space).
+ * p_xz, m; rates s_e = 1.19, s_eps = 1.4, s_q = 1.99, s_m = 1.98, and the
+ * five stress moments 3p_xx, p_ww, p_xy, p_yz, p_xz with the two pi moments
+ * 3pi_xx, pi_ww at 1/tau_eff (d'Humieres' s_q = 1.2 and s_pi = 1.4 make the
+ * scheme linearly unstable at the tau0 of the channels, tau0 - 1/2 ~ 1e-4);
+ * equilibrium moments M f^eq; Guo forcing in moment space).
  * Both use the Smagorinsky tau_eff. u_tau_ref > 0 and a_plus > 0 add van Driest
  * damping of the Smagorinsky length, C_s (1 - exp(-y+/A+)), with y the layer
  * centre's distance to the nearer wall (j + 1/2) and y+ = y u_tau_ref / nu (nu
@@ -284,12 +292,14 @@ int lbm_conservation(lbm_handle *h, double *out);
  * Asynchronous on the handle's stream. The block partial sums live in one
  * fixed array of 1.44 MB that the library keeps in device memory on every GPU
  * that loads it, until the process exits; it holds at most ny = 2048 layers,
- * and larger grids are rejected with LBM_ERR_ARG. The first call on a device
- * looks up that array's device address (cudaGetSymbolAddress) with the device
- * current, so make the first call before any stream capture. Every call
- * overwrites the part of the array it uses, so nothing needs clearing between
- * calls; calls whose work overlaps on the GPU (other streams or handles) race
- * on the shared array and must be ordered by the caller. */
+ * and larger grids are rejected with LBM_ERR_ARG. The array used is the one of
+ * the CURRENT device, so the handle's device must be current when calling. The
+ * first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress) with the device current, so make the first call
+ * before any stream capture. Every call overwrites the part of the array it
+ * uses, so nothing needs clearing between calls; calls whose work overlaps on
+ * the GPU (other streams or handles) race on the shared array and must be
+ * ordered by the caller. */
 int lbm_plane_profile_noalloc(lbm_handle *h, double *out_dev);
 
 /* ---------------------------------------------------------------------------
@@ -329,23 +339,48 @@ long long lbm_batch_cells(lbm_batch *b);
  * `every` (0 = never), accumulated in each member's lbm_plane_stats. */
 int lbm_batch_set_stats_every(lbm_batch *b, int every);
 
-/* Advance every member by n steps: one launch of the persistent batch kernel
- * per step over the work list of all members' tiles. Asynchronous. */
+/* Advance every member by n steps. Asynchronous. */
 int lbm_batch_step(lbm_batch *b, int n);
 
-/* Launch shape: threads per CTA (64 or 128; a tile is 2 * threads cells of one
- * row) and CTAs per SM (<= 0 or above the occupancy limit selects the limit). */
+/* Form of the batch step (no counterpart in the paper; both give every member
+ * bitwise the populations of the same channel run alone with the kernel named
+ * below):
+ *   PERSISTENT     one launch of the persistent batch kernel per step over the
+ *                  work list of all members' two-cell tiles (any even nx; the
+ *                  members run the PAIR kernel's arithmetic).
+ *   MEMBER_GRIDS   every member runs the single-channel step kernels its grid
+ *                  selects (AUTO: QUAD for FP16 storage and nx a multiple of
+ *                  4, else PAIR), its members spread over `streams` capture
+ *                  streams (1 .. 32; 0 selects 8) balanced by cell count, and
+ *                  each 16-step chunk of all members captured as one CUDA
+ *                  graph, so that the members' grids run concurrently.
+ * lbm_batch_create selects MEMBER_GRIDS (8 streams); the autotuner searches
+ * both. */
+typedef enum {
+    LBM_BATCH_PERSISTENT = 1,
+    LBM_BATCH_MEMBER_GRIDS = 2
+} lbm_batch_form;
+
+/* Select the form (and, for MEMBER_GRIDS, the number of capture streams).
+ * Synchronises; the state is kept. LBM_ERR_ARG for an unknown form or a
+ * stream count outside 0 .. 32. */
+int lbm_batch_set_form(lbm_batch *b, int form, int streams);
+
+/* The form in use (-1 for a NULL batch); *streams (nullable) receives the
+ * capture streams of the member-grid form. */
+int lbm_batch_get_form(lbm_batch *b, int *streams);
+
+/* Launch shape of the persistent form: threads per CTA (64 or 128; a tile is
+ * 2 * threads cells of one row) and CTAs per SM (<= 0 or above the occupancy
+ * limit selects the limit). */
 int lbm_batch_set_config(lbm_batch *b, int threads, int ctas_per_sm);
 int lbm_batch_get_config(lbm_batch *b, int *threads, int *ctas_per_sm, int *grid, long long *tiles);
 
-/* LES model of every member (see lbm_set_les): one collision operator for the
- * batch; u_tau_ref [n] (host, may be NULL: no damping) per member and a_plus. */
-int lbm_batch_set_les(lbm_batch *b, int collision, const double *u_tau_ref, double a_plus);
-
-/* Time every launch shape for `steps` steps (after 2 warm-up steps) and keep
- * the fastest; best_ms (nullable) receives its time per step. The timed steps
- * advance all members like lbm_batch_step, so tune before initialising the
- * members. Synchronises. */
+/* Time every form (lbm_batch_set_form) with its launch shapes (threads per
+ * CTA x CTAs per SM; 4, 8 or 16 streams) for `steps` steps each (after 2
+ * warm-up steps) and keep the fastest; best_ms (nullable) receives its time
+ * per step. The timed steps advance all members like lbm_batch_step, so tune
+ * before initialising the members. Synchronises. */
 int lbm_batch_autotune(lbm_batch *b, int steps, double *best_ms);
 
 /* Block until the batch's work has finished. */
@@ -356,8 +391,19 @@ void lbm_batch_destroy(lbm_batch *b);
 
 /* Block until all work queued on the handle's stream has finished. Returns
  * LBM_ERR_CUDA if a wait inside the pipelined kernel timed out (the kernel then
- * stops early and leaves the step incomplete). */
+ * stops early and leaves the step incomplete, so the populations are no longer
+ * a valid state). A timeout is reported once: the call clears the device flag
+ * after reading it, so the next call succeeds unless another wait timed out. */
 int lbm_sync(lbm_handle *h);
+
+/* Clock cycles each shared-memory pipeline wait of the pipelined (TMA) kernel
+ * may take before it gives up and sets the error flag that lbm_sync reports
+ * (failure detection, no counterpart in the paper). cycles <= 0 restores the
+ * default of 2^32 (about 2 s at 2 GHz). Whatever the limit, a CTA that gives
+ * up first waits, for at most the default, until the copies it has issued have
+ * landed, so that none arrives after it has exited. Other kernel forms have
+ * no waits. Synchronises the stream and drops the captured step graphs. */
+int lbm_set_wait_limit(lbm_handle *h, long long cycles);
 
 /* Free every device resource of the handle. NULL is ignored. */
 void lbm_destroy(lbm_handle *h);

@@ -1,7 +1,8 @@
 """Launch-shape autotuning of the batched ensemble, with a JSON cache.
 
-The timing itself runs in the library (lbm_batch_autotune tries every
-(threads per CTA, CTAs per SM) shape and keeps the fastest); this module
+The timing itself runs in the library (lbm_batch_autotune tries both batch
+forms, the persistent kernel at every (threads per CTA, CTAs per SM) shape and
+the member grids on 4, 8 and 16 streams, and keeps the fastest); this module
 remembers the winner per (GPU, storage precision, member grids) so that later
 runs apply it without re-timing.
 """
@@ -39,13 +40,15 @@ def tune_batch(batch, cache_path: str | None = None, steps: int = 3, retune: boo
     path = cache_path or DEFAULT_CACHE
     cache = _load(path)
     key = batch_key(batch)
-    if key in cache and not retune:
+    if key in cache and not retune and "streams" in cache[key]:
         cfg = cache[key]
+        batch.set_form(cfg["form"], cfg["streams"])
         batch.set_config(cfg["threads"], cfg["ctas_per_sm"])
         return {**cfg, "cached": True}
     ms = batch.autotune(steps)
     c = batch.config()
-    cfg = {"threads": c["threads"], "ctas_per_sm": c["ctas_per_sm"], "ms_per_step": ms}
+    cfg = {"form": c["form"], "streams": c["streams"], "threads": c["threads"], "ctas_per_sm": c["ctas_per_sm"],
+           "ms_per_step": ms}
     cache[key] = cfg
     os.makedirs(os.path.dirname(path), exist_ok=True)
     tmp = f"{path}.tmp{os.getpid()}"

@@ -91,12 +91,18 @@ int select_kernel(lbm_handle *h, int kernel)
     return LBM_OK;
 }
 
+// Read (and clear) the device flag of a timed-out pipeline wait: a timeout is
+// reported once, by the first synchronising call after it.
 int check_err(lbm_handle *h)
 {
     int e = 0;
     CK(cudaMemcpyAsync(&e, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
-    if (e) return fail(LBM_ERR_CUDA, "a pipeline wait in the step kernel timed out");
+    if (e) {
+        CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        return fail(LBM_ERR_CUDA, "a pipeline wait in the step kernel timed out");
+    }
     return LBM_OK;
 }
 
@@ -132,10 +138,10 @@ void launch_rows_t(lbm_handle *h, cudaStream_t s, int src, bool stats)
     const dim3 grid(h->tma_grid), block(NW * 32);
     if (stats)
         lbm::k_step_rows<T, true, NW, COLL><<<grid, block, h->tma_smem, s>>>(a, b, h->g, h->p, h->tw, h->part, h->err,
-                                                                              h->tma_stages);
+                                                                              h->tma_stages, h->wait_limit);
     else
         lbm::k_step_rows<T, false, NW, COLL><<<grid, block, h->tma_smem, s>>>(a, b, h->g, h->p, h->tw, h->part,
-                                                                               h->err, h->tma_stages);
+                                                                               h->err, h->tma_stages, h->wait_limit);
 }
 
 // Blocks per SM of one row-kernel instantiation with `smem` dynamic bytes.
@@ -211,6 +217,8 @@ cudaError_t launch_aa(lbm_handle *h, cudaStream_t s, bool stats)
     const dim3 grid = step_grid(h), block(h->bx);
     void *f = h->f[0];
     if (h->kernel == LBM_KERNEL_QUAD) {
+        // one launch over every row (an interior / wall-row split, as in the
+        // two-lattice step, measured slower for the in-place steps)
         __half *fh = (__half *)f;
         return stats ? launch_pdl(lbm::k_step_quad_aa<true, COLL, LAY>, grid, block, 0, s, fh, h->g, h->p, h->tw, h->part)
                      : launch_pdl(lbm::k_step_quad_aa<false, COLL, LAY>, grid, block, 0, s, fh, h->g, h->p, h->tw,
@@ -285,12 +293,13 @@ int launch_step_c(lbm_handle *h, cudaStream_t s, int src, bool stats)
                       : launch_pdl(lbm::k_step_quad<false, COLL, lbm::ROWS_INTERIOR>, gi, block, 0, s, ah, bh, h->g,
                                    h->p, h->tw, h->part);
         }
-        const dim3 gw(grid.x, 2, grid.z);
+        // the wall rows with the two-cell tile in CTAs of twice the threads
+        const dim3 gw(grid.x, 2, grid.z), bw(2 * h->bx);
         if (COLL == lbm::COLL_BGK && e == cudaSuccess)
-            e = stats ? launch_pdl(lbm::k_step_quad<true, COLL, lbm::ROWS_WALL>, gw, block, 0, s, ah, bh, h->g, h->p,
-                                   h->tw, h->part)
-                      : launch_pdl(lbm::k_step_quad<false, COLL, lbm::ROWS_WALL>, gw, block, 0, s, ah, bh, h->g, h->p,
-                                   h->tw, h->part);
+            e = stats ? launch_pdl(lbm::k_step_pair_wall<__half, true, COLL>, gw, bw, 0, s, ah, bh, h->g, h->p, h->tw,
+                                   h->part)
+                      : launch_pdl(lbm::k_step_pair_wall<__half, false, COLL>, gw, bw, 0, s, ah, bh, h->g, h->p, h->tw,
+                                   h->part);
     } else if (h->kernel == LBM_KERNEL_PAIR) {
         if (half) {
             const __half *ah = (const __half *)a;
@@ -354,6 +363,22 @@ int build_chunk(lbm_handle *h, int start)
     e = cudaGraphInstantiate(&h->chunk[start], graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    // move the graph's device-side set-up off its first launch
+    e = cudaGraphUpload(h->chunk[start], h->stream);
+    if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "graph upload: %s", cudaGetErrorString(e));
+    return LBM_OK;
+}
+
+// Both chunk graphs (start phase 0 and 1), built together on the first step
+// call after any change that invalidated them, whatever the step count, so that
+// no capture or instantiation falls inside a later, longer run of steps.
+int ensure_chunks(lbm_handle *h)
+{
+    for (int start = 0; start < 2; ++start)
+        if (!h->chunk[start]) {
+            const int rc = build_chunk(h, start);
+            if (rc != LBM_OK) return rc;
+        }
     return LBM_OK;
 }
 
@@ -403,15 +428,20 @@ const char *lbm_last_error(void) { return g_err; }
 
 }  // extern "C"
 
+int lbm_launch_step(lbm_handle *h, cudaStream_t s, int src, bool stats) { return launch_step(h, s, src, stats); }
+
 int lbm_create_handle(lbm_grid g, double tau, double C_s, const double force[3], lbm_wall_model wm, int precision,
                       int layout, void *cuda_stream, void *pop0, void *pop1, lbm_handle **out)
 {
+    LbmRange range("lbm_create");
     if (!out) return fail(LBM_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (g.nx < 1 || g.ny < 2 || g.nz < 1) return fail(LBM_ERR_ARG, "grid needs nx >= 1, ny >= 2, nz >= 1");
     if (!(tau > 0.5)) return fail(LBM_ERR_ARG, "tau must exceed 1/2");
     if (!(C_s >= 0.0)) return fail(LBM_ERR_ARG, "C_s must be >= 0");
     if (!force) return fail(LBM_ERR_ARG, "force is NULL");
+    if (!isfinite(force[0]) || !isfinite(force[1]) || !isfinite(force[2]))
+        return fail(LBM_ERR_ARG, "force must be finite");
     if (wm.kind < LBM_WALL_BB || wm.kind > LBM_WALL_WFB_NODE) return fail(LBM_ERR_ARG, "unknown wall kind");
     if (wm.kind == LBM_WALL_WFB_NODE && g.ny < 3) return fail(LBM_ERR_ARG, "wall nodes need ny >= 3");
     if (wm.kind == LBM_WALL_WFB_NODE && layout == LBM_AA)
@@ -468,6 +498,7 @@ int lbm_create_handle(lbm_grid g, double tau, double C_s, const double force[3],
         const int a = 2 * k + 1;
         const double eF = lbm::ex_of(a) * force[0] + lbm::ey_of(a) * force[1] + lbm::ez_of(a) * force[2];
         h->p.weF[k] = (float)(lbm::w_of(a) * eF);
+        h->p.WeF[k] = (float)(36.0 * lbm::w_of(a) * eF);
     }
     h->p.t02 = (float)((double)h->p.tau0 * (double)h->p.tau0);
     h->nu_wall = nu;
@@ -498,6 +529,7 @@ int lbm_create_handle(lbm_grid g, double tau, double C_s, const double force[3],
     h->layout = layout;
     h->stream = (cudaStream_t)cuda_stream;
     h->pair = (g.nx % 2) == 0;
+    h->wait_limit = lbm::WAIT_CYCLES;
 
     auto bail = [&](int rc) {
         lbm_free_handle(h);
@@ -619,6 +651,7 @@ int lbm_init_channel(lbm_handle *h, const double *u_mean_x, double noise_amp, ui
 
 int lbm_set_populations(lbm_handle *h, const double *host_in)
 {
+    LbmRange range("lbm_set_populations");
     if (!h || !host_in) return fail(LBM_ERR_ARG, "NULL argument");
     const size_t b = (size_t)lbm::Q * h->g.nx * h->g.ny * h->g.nz * sizeof(double);
     double *d = nullptr;
@@ -640,6 +673,7 @@ int lbm_set_populations(lbm_handle *h, const double *host_in)
 
 int lbm_populations(lbm_handle *h, double *host_out)
 {
+    LbmRange range("lbm_populations");
     if (!h || !host_out) return fail(LBM_ERR_ARG, "NULL argument");
     const size_t b = (size_t)lbm::Q * h->g.nx * h->g.ny * h->g.nz * sizeof(double);
     double *d = nullptr;
@@ -660,8 +694,13 @@ int lbm_set_stats_every(lbm_handle *h, int every)
 
 int lbm_step(lbm_handle *h, int n)
 {
+    LbmRange range("lbm_step");
     if (!h || n < 0) return fail(LBM_ERR_ARG, "invalid argument");
     if (h->member) return fail(LBM_ERR_STATE, "a batch member is advanced by lbm_batch_step");
+    if (n > 0) {
+        const int rc = ensure_chunks(h);
+        if (rc != LBM_OK) return rc;
+    }
     while (n > 0) {
         const bool sample = h->stats_every > 0 && (h->step % h->stats_every) == 0;
         if (sample) {
@@ -679,10 +718,6 @@ int lbm_step(lbm_handle *h, int n)
             if (to_next < run) run = to_next;
         }
         while (run >= kGraphSteps) {
-            if (!h->chunk[h->cur]) {
-                int rc = build_chunk(h, h->cur);
-                if (rc != LBM_OK) return rc;
-            }
             CK(cudaGraphLaunch(h->chunk[h->cur], h->stream));
             h->step += kGraphSteps;
             run -= kGraphSteps;
@@ -724,6 +759,7 @@ int lbm_set_les(lbm_handle *h, int collision, double u_tau_ref, double a_plus)
 
 int lbm_moments(lbm_handle *h, float *rho, float *u, int on_device)
 {
+    LbmRange range("lbm_moments");
     if (!h) return fail(LBM_ERR_ARG, "NULL handle");
     if (!rho && !u) return LBM_OK;
     if (on_device) return export_state(h, rho, u, nullptr, nullptr);
@@ -751,6 +787,7 @@ int lbm_wall_stress(lbm_handle *h, float *tau, int on_device)
 
 int lbm_plane_stats(lbm_handle *h, double *out, double *wall_out, long long *n_samples, int reset)
 {
+    LbmRange range("lbm_plane_stats");
     if (!h) return fail(LBM_ERR_ARG, "NULL handle");
     const size_t b = (size_t)h->g.ny * lbm::K_STATS * sizeof(double);
     if (out) CK(cudaMemcpyAsync(out, h->acc, b, cudaMemcpyDeviceToHost, h->stream));
@@ -768,6 +805,7 @@ int lbm_plane_stats(lbm_handle *h, double *out, double *wall_out, long long *n_s
 
 int lbm_conservation(lbm_handle *h, double *out)
 {
+    LbmRange range("lbm_conservation");
     if (!h || !out) return fail(LBM_ERR_ARG, "NULL argument");
     const dim3 grid = grid_of(h, 128);
     const long long nblk = (long long)grid.x * grid.y * grid.z;
@@ -786,6 +824,20 @@ int lbm_conservation(lbm_handle *h, double *out)
     out[0] += (double)h->g.nx * h->g.ny * h->g.nz;
     for (int k = 0; k < 4; ++k)
         if (!isfinite(out[k])) return fail(LBM_ERR_DIVERGED, "non-finite conservation sum (component %d)", k);
+    return LBM_OK;
+}
+
+int lbm_set_wait_limit(lbm_handle *h, long long cycles)
+{
+    if (!h) return fail(LBM_ERR_ARG, "NULL handle");
+    CK(cudaStreamSynchronize(h->stream));
+    h->wait_limit = cycles > 0 ? cycles : lbm::WAIT_CYCLES;
+    // captured graphs hold the old limit
+    for (int i = 0; i < 2; ++i)
+        if (h->chunk[i]) {
+            cudaGraphExecDestroy(h->chunk[i]);
+            h->chunk[i] = nullptr;
+        }
     return LBM_OK;
 }
 

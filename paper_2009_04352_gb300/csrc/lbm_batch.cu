@@ -1,17 +1,25 @@
 // Batched ensemble: many independent channels of uneven sizes and parameters
-// advanced by ONE persistent kernel launch per time step.
+// advanced together, each step replayed from CUDA graphs. Two forms:
 //
-// All members' lattices live in one device pool. The work list is the
-// concatenation of every member's tiles (a tile = 2 * threads consecutive
-// cells of one (y, z) row, the unit of the two-cell kernel); member i owns
-// tiles [tile0_i, tile0_i + tiles_i). A grid of CTAs sized to the GPU
-// (CTAs per SM x SM count) splits the list into contiguous shares; a CTA finds
-// the member of its first tile by binary search over tile0, stages the
-// member's descriptor (geometry, physics, pool offsets) in shared memory, and
-// then advances (tile, row, member) incrementally, running the same tile code
-// as the single-channel kernel. Plain steps are replayed from a
-// CUDA graph of 16 steps; sampled steps add one plane reduction per member.
-// The launch shape (threads per CTA, CTAs per SM) is chosen by a timing
+// * Persistent form: ONE persistent kernel launch per time step. All members'
+//   lattices live in one device pool. The work list is the concatenation of
+//   every member's tiles (a tile = 2 * threads consecutive cells of one (y, z)
+//   row, the unit of the two-cell kernel); member i owns tiles [tile0_i,
+//   tile0_i + tiles_i). A grid of CTAs sized to the GPU (CTAs per SM x SM
+//   count) splits the list into contiguous shares; a CTA finds the member of
+//   its first tile by binary search over tile0, stages the member's descriptor
+//   (geometry, physics, pool offsets) in shared memory, and then advances
+//   (tile, row, member) incrementally, running the same tile code as the
+//   single-channel kernel.
+// * Member-grid form: every member runs the single-channel step kernels its
+//   own grid selects (four-cell for FP16 storage, two-cell for FP32), with
+//   its geometry and physics as launch parameters; the members are spread
+//   over a few capture streams balanced by cell count and each 16-step chunk
+//   of all members is captured as one CUDA graph, so the members' grids run
+//   concurrently and small members fill the gaps of large ones.
+//
+// Sampled steps add one plane reduction per member. The form and its launch
+// shape (threads per CTA and CTAs per SM, or streams) are chosen by a timing
 // autotuner.
 #include <math.h>
 #include <stdio.h>
@@ -27,6 +35,7 @@
 namespace {
 
 constexpr int kBatchGraphSteps = 16;
+constexpr int kMaxStreams = 32;   // capture streams of the member-grid form
 
 struct BatchInst {
     lbm::Geom g;
@@ -133,10 +142,15 @@ struct lbm_batch {
     std::vector<long long> off;   // per member: offset of lattice 0 (lattice 1 follows)
     BatchInst *d_inst;
     long long tiles;
+    int form;                     // LBM_BATCH_PERSISTENT or LBM_BATCH_MEMBER_GRIDS
     int threads;                  // threads per CTA (tile = 2 * threads cells)
     int ctas_per_sm;
     int grid;
     int sms;
+    int nstreams;                 // member-grid form: capture streams in use
+    cudaStream_t side[kMaxStreams];
+    cudaEvent_t fork, join[kMaxStreams];
+    std::vector<int> lane;        // member-grid form: capture stream of each member
     int cur;
     long long step;
     int stats_every;
@@ -225,8 +239,35 @@ cudaError_t launch_pdl(lbm_batch *b, cudaStream_t s, int cur)
                               (T *)b->pool, cur);
 }
 
+// Member-grid form: spread the members over `streams` capture streams,
+// largest first onto the least loaded.
+void assign_streams(lbm_batch *b, int streams)
+{
+    b->nstreams = streams;
+    std::vector<int> order(b->n);
+    for (int i = 0; i < b->n; ++i) order[i] = i;
+    auto cells = [&](int i) { return (long long)b->members[i]->g.nx * b->members[i]->g.ny * b->members[i]->g.nz; };
+    std::sort(order.begin(), order.end(), [&](int x, int y) { return cells(x) > cells(y); });
+    std::vector<long long> load(streams, 0);
+    b->lane.assign(b->n, 0);
+    for (int i : order) {
+        const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        b->lane[i] = k;
+        load[k] += cells(i);
+    }
+}
+
 int launch(lbm_batch *b, cudaStream_t s, int cur, bool stats)
 {
+    if (b->form == LBM_BATCH_MEMBER_GRIDS) {
+        // one member after the other on s (the graphs of plain steps run the
+        // members on their capture streams instead)
+        for (lbm_handle *m : b->members) {
+            const int rc = lbm_launch_step(m, s, cur, stats);
+            if (rc != LBM_OK) return rc;
+        }
+        return LBM_OK;
+    }
     cudaError_t e;
     const bool mrt = b->members[0]->p.collision == lbm::COLL_MRT;
     if (b->precision == LBM_FP16_SHIFTED) {
@@ -258,7 +299,23 @@ int build_chunk(lbm_batch *b, int start)
     cudaGraph_t graph = nullptr;
     BK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
     int rc = LBM_OK;
-    for (int i = 0; i < kBatchGraphSteps && rc == LBM_OK; ++i) rc = launch(b, b->cap, start ^ (i & 1), false);
+    if (b->form == LBM_BATCH_MEMBER_GRIDS) {
+        // fork to the capture streams, each runs its members' 16 steps in
+        // step order, join
+        cudaError_t ce = cudaEventRecord(b->fork, b->cap);
+        for (int k = 0; k < b->nstreams && ce == cudaSuccess; ++k) ce = cudaStreamWaitEvent(b->side[k], b->fork, 0);
+        if (ce != cudaSuccess) rc = fail_cuda(ce, "graph fork");
+        for (int i = 0; i < kBatchGraphSteps && rc == LBM_OK; ++i)
+            for (int m = 0; m < b->n && rc == LBM_OK; ++m)
+                rc = lbm_launch_step(b->members[m], b->side[b->lane[m]], start ^ (i & 1), false);
+        for (int k = 0; k < b->nstreams && ce == cudaSuccess; ++k) {
+            ce = cudaEventRecord(b->join[k], b->side[k]);
+            if (ce == cudaSuccess) ce = cudaStreamWaitEvent(b->cap, b->join[k], 0);
+        }
+        if (ce != cudaSuccess && rc == LBM_OK) rc = fail_cuda(ce, "graph join");
+    } else {
+        for (int i = 0; i < kBatchGraphSteps && rc == LBM_OK; ++i) rc = launch(b, b->cap, start ^ (i & 1), false);
+    }
     cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
     if (rc != LBM_OK) {
         if (graph) cudaGraphDestroy(graph);
@@ -268,6 +325,20 @@ int build_chunk(lbm_batch *b, int start)
     e = cudaGraphInstantiate(&b->chunk[start], graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return fail_cuda(e, "graph instantiate");
+    e = cudaGraphUpload(b->chunk[start], b->stream);
+    if (e != cudaSuccess) return fail_cuda(e, "graph upload");
+    return LBM_OK;
+}
+
+// Both chunk graphs, built on the first step call after a reconfiguration
+// (whatever its step count), so that no capture lands inside a later run.
+int ensure_chunks(lbm_batch *b)
+{
+    for (int start = 0; start < 2; ++start)
+        if (!b->chunk[start]) {
+            const int rc = build_chunk(b, start);
+            if (rc != LBM_OK) return rc;
+        }
     return LBM_OK;
 }
 
@@ -285,6 +356,7 @@ extern "C" {
 
 int lbm_batch_create(int n, const lbm_member *members, int precision, void *cuda_stream, lbm_batch **out)
 {
+    LbmRange range("lbm_batch_create");
     if (!out) return fail(LBM_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (n < 1 || !members) return fail(LBM_ERR_ARG, "a batch needs n >= 1 members");
@@ -300,6 +372,12 @@ int lbm_batch_create(int n, const lbm_member *members, int precision, void *cuda
     b->pool = nullptr;
     b->d_inst = nullptr;
     b->cap = nullptr;
+    b->fork = nullptr;
+    b->nstreams = 0;
+    for (int k = 0; k < kMaxStreams; ++k) {
+        b->side[k] = nullptr;
+        b->join[k] = nullptr;
+    }
     auto bail = [&](int rc) {
         lbm_batch_destroy(b);
         return rc;
@@ -310,6 +388,12 @@ int lbm_batch_create(int n, const lbm_member *members, int precision, void *cuda
         return bail(fail(LBM_ERR_CUDA, "cannot query the device"));
     if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess)
         return bail(fail(LBM_ERR_CUDA, "cannot create capture stream"));
+    if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess)
+        return bail(fail(LBM_ERR_CUDA, "cannot create capture events"));
+    for (int k = 0; k < kMaxStreams; ++k)
+        if (cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming) != cudaSuccess)
+            return bail(fail(LBM_ERR_CUDA, "cannot create capture streams"));
     // pool layout: per member two lattices of 19 row-padded planes, 256-byte aligned
     const size_t eb = elem_bytes(precision);
     long long total = 0;
@@ -347,6 +431,8 @@ int lbm_batch_create(int n, const lbm_member *members, int precision, void *cuda
     b->cur = 0;
     b->step = 0;
     b->stats_every = 0;
+    b->form = LBM_BATCH_MEMBER_GRIDS;   // measured faster than the persistent form on GB300
+    assign_streams(b, 8);
     const int rc = configure(b, 128, 0);
     if (rc != LBM_OK) return bail(rc);
     *out = b;
@@ -376,7 +462,12 @@ int lbm_batch_set_stats_every(lbm_batch *b, int every)
 
 int lbm_batch_step(lbm_batch *b, int n)
 {
+    LbmRange range("lbm_batch_step");
     if (!b || n < 0) return fail(LBM_ERR_ARG, "invalid argument");
+    if (n > 0) {
+        const int rc = ensure_chunks(b);
+        if (rc != LBM_OK) return rc;
+    }
     while (n > 0) {
         const bool sample = b->stats_every > 0 && (b->step % b->stats_every) == 0;
         if (sample) {
@@ -391,10 +482,6 @@ int lbm_batch_step(lbm_batch *b, int n)
         long long run = n;
         if (b->stats_every > 0) run = std::min<long long>(run, b->stats_every - (b->step % b->stats_every));
         while (run >= kBatchGraphSteps) {
-            if (!b->chunk[b->cur]) {
-                const int rc = build_chunk(b, b->cur);
-                if (rc != LBM_OK) return rc;
-            }
             BK(cudaGraphLaunch(b->chunk[b->cur], b->stream));
             b->step += kBatchGraphSteps;
             run -= kBatchGraphSteps;
@@ -429,42 +516,77 @@ int lbm_batch_get_config(lbm_batch *b, int *threads, int *ctas_per_sm, int *grid
     return LBM_OK;
 }
 
+int lbm_batch_set_form(lbm_batch *b, int form, int streams)
+{
+    if (!b) return fail(LBM_ERR_ARG, "NULL batch");
+    if (form != LBM_BATCH_PERSISTENT && form != LBM_BATCH_MEMBER_GRIDS) return fail(LBM_ERR_ARG, "unknown batch form");
+    if (streams < 0 || streams > kMaxStreams) return fail(LBM_ERR_ARG, "streams must be 0 .. 32");
+    BK(cudaStreamSynchronize(b->stream));
+    b->form = form;
+    assign_streams(b, streams == 0 ? 8 : streams);
+    drop_graphs(b);
+    return LBM_OK;
+}
+
+int lbm_batch_get_form(lbm_batch *b, int *streams)
+{
+    if (!b) return -1;
+    if (streams) *streams = b->nstreams;
+    return b->form;
+}
+
 int lbm_batch_autotune(lbm_batch *b, int steps, double *best_ms)
 {
+    LbmRange range("lbm_batch_autotune");
     if (!b || steps < 1) return fail(LBM_ERR_ARG, "invalid argument");
     cudaEvent_t e0, e1;
     BK(cudaEventCreate(&e0));
     BK(cudaEventCreate(&e1));
     double best = 1e300;
-    int best_t = 128, best_c = 0;
+    int best_form = LBM_BATCH_PERSISTENT, best_t = 128, best_c = 0, best_s = 8;
     const int saved_stats = b->stats_every;
     b->stats_every = 0;
+    auto time_shape = [&](int form, int threads, int c, int streams) -> int {
+        b->form = form;
+        assign_streams(b, streams);
+        int rc = configure(b, threads, c);
+        if (rc == LBM_OK) rc = lbm_batch_step(b, 2);   // warm-up (builds the step graphs)
+        if (rc != LBM_OK) return rc;
+        BK(cudaEventRecord(e0, b->stream));
+        rc = lbm_batch_step(b, steps);
+        if (rc != LBM_OK) return rc;
+        BK(cudaEventRecord(e1, b->stream));
+        BK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        BK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) {
+            best = ms;
+            best_form = form;
+            best_t = threads;
+            best_c = c;
+            best_s = streams;
+        }
+        return LBM_OK;
+    };
     for (int threads : {64, 128}) {
         int max_per_sm = 0;
         int rc = max_ctas_per_sm(b, threads, &max_per_sm);
         if (rc != LBM_OK) return rc;
         for (int c = std::max(1, max_per_sm / 4); c <= max_per_sm; c += std::max(1, max_per_sm / 4)) {
-            rc = configure(b, threads, c);
-            if (rc == LBM_OK) rc = lbm_batch_step(b, 2);   // warm-up
+            rc = time_shape(LBM_BATCH_PERSISTENT, threads, c, b->nstreams);
             if (rc != LBM_OK) return rc;
-            BK(cudaEventRecord(e0, b->stream));
-            rc = lbm_batch_step(b, steps);
-            if (rc != LBM_OK) return rc;
-            BK(cudaEventRecord(e1, b->stream));
-            BK(cudaEventSynchronize(e1));
-            float ms = 0.f;
-            BK(cudaEventElapsedTime(&ms, e0, e1));
-            if (ms < best) {
-                best = ms;
-                best_t = threads;
-                best_c = c;
-            }
         }
+    }
+    for (int streams : {4, 8, 16}) {
+        const int rc = time_shape(LBM_BATCH_MEMBER_GRIDS, b->threads, b->ctas_per_sm, std::min(streams, b->n));
+        if (rc != LBM_OK) return rc;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     b->stats_every = saved_stats;
     if (best_ms) *best_ms = best / steps;
+    b->form = best_form;
+    assign_streams(b, best_s);
     return configure(b, best_t, best_c);
 }
 
@@ -492,6 +614,11 @@ void lbm_batch_destroy(lbm_batch *b)
     if (!b) return;
     cudaStreamSynchronize(b->stream);
     drop_graphs(b);
+    for (int k = 0; k < kMaxStreams; ++k) {
+        if (b->side[k]) cudaStreamDestroy(b->side[k]);
+        if (b->join[k]) cudaEventDestroy(b->join[k]);
+    }
+    if (b->fork) cudaEventDestroy(b->fork);
     for (lbm_handle *m : b->members) lbm_free_handle(m);
     if (b->d_inst) cudaFree(b->d_inst);
     if (b->pool) cudaFree(b->pool);

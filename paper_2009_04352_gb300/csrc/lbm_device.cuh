@@ -97,6 +97,7 @@ struct Phys {
     // derived on the host once, so kernels do not recompute them per tile
     float hF[3];         // F / 2
     float weF[9];        // w_k (e_k . F) for the opposite pairs k = 0..8 (directions 2k+1, 2k+2)
+    float WeF[9];        // 36 w_k (e_k . F), the same with the weights scaled by 36
     float t02;           // tau0^2
     // LES model
     int collision;       // COLL_BGK or COLL_MRT
@@ -351,12 +352,15 @@ __device__ __forceinline__ Moments moments_of(const float (&f)[Q])
 // increasing and convex, so any start at or above the root descends
 // monotonically. The start is the laminar guess sqrt(R), lowered for R > 100
 // to the log-law bound ln(R)/kappa + B, which also lies above the root and
-// saves the slow exponential-regime steps. All lanes of the warp iterate
-// together and stop when every lane's relative step is below 1e-7.
+// saves the slow exponential-regime steps. Each lane keeps its value once its
+// own relative step is below 1e-7, so a cell's result does not depend on which
+// cells share its warp (every kernel form gives the same bits); the warp
+// leaves the loop when all its lanes have stopped.
 __device__ __forceinline__ float spalding_uplus(float R, const Phys &p, unsigned mask)
 {
     float up = sqrtf(R);
     if (R > 100.f) up = fminf(up, __fadd_rn(logf(R) / p.kappa, p.B));
+    bool done = false;
     for (int it = 0; it < p.newton_iters; ++it) {
         const float k = p.kappa * up;
         const float ek = expf(k);
@@ -365,9 +369,9 @@ __device__ __forceinline__ float spalding_uplus(float R, const Phys &p, unsigned
         const float t3 = __fsub_rn(t2, __fmul_rn(__fmul_rn(k2, k), 1.f / 6.f));            // ... - k^3/6
         const float S = __fmaf_rn(p.ekb, t3, up);                                           // y+(u+)
         const float dS = __fmaf_rn(__fmul_rn(p.ekb, p.kappa), t2, 1.f);                     // dy+/du+
-        const float step = __fmaf_rn(up, S, -R) / __fmaf_rn(up, dS, S);
+        const float step = done ? 0.f : __fmaf_rn(up, S, -R) / __fmaf_rn(up, dS, S);
         up -= step;
-        const bool done = fabsf(step) <= 1e-7f * up;
+        done = done || fabsf(step) <= 1e-7f * up;
         if (__all_sync(mask, done)) break;
     }
     return up;
@@ -377,18 +381,19 @@ __device__ __forceinline__ float spalding_uplus(float R, const Phys &p, unsigned
 // u+ + (ln u+ - ln R) / kappa - B = 0. That function is concave and increasing,
 // so Newton from the left of the root climbs to it monotonically; the start,
 // one fixed-point step from the log law at y+ = R, lies left of the root for
-// every R above the crossing. Same warp-wide stop as spalding_uplus.
+// every R above the crossing. Same per-lane stop as spalding_uplus.
 __device__ __forceinline__ float loglaw_uplus(float R, const Phys &p, unsigned mask)
 {
     const bool visc = R <= p.law_r2;
     const float lr = logf(fmaxf(R, p.law_r2));
     const float u0 = __fmaf_rn(lr, p.ikappa, p.B);
     float up = __fmaf_rn(-logf(u0), p.ikappa, u0);
+    bool done = visc;
     for (int it = 0; it < p.newton_iters; ++it) {
         const float h = __fsub_rn(__fmaf_rn(__fsub_rn(logf(up), lr), p.ikappa, up), p.B);
-        const float step = h / __fadd_rn(1.f, p.ikappa / up);
+        const float step = done ? 0.f : h / __fadd_rn(1.f, p.ikappa / up);
         up -= step;
-        const bool done = visc || fabsf(step) <= 1e-7f * up;
+        done = done || fabsf(step) <= 1e-7f * up;
         if (__all_sync(mask, done)) break;
     }
     return visc ? sqrtf(R) : up;

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "lbm.h"
 #include "lbm_device.cuh"
@@ -31,6 +32,7 @@ struct lbm_handle {
     int tma_stages;              // ring stages of the row-pipelined kernel
     int tma_smem;                // dynamic shared memory bytes of the row-pipelined kernel
     int *err;                    // device flag set by a timed-out pipeline wait
+    long long wait_limit;        // clock cycles a pipeline wait may take before it gives up
     cudaGraphExec_t chunk[2];    // kGraphSteps plain steps starting from cur = 0 / 1
     bool member;                 // member view of a batch (stepped by the batch)
     bool borrowed;               // population arrays owned by the caller or a batch, not freed here
@@ -58,5 +60,18 @@ int lbm_create_handle(lbm_grid g, double tau, double C_s, const double force[3],
 // Free a handle, member views included.
 void lbm_free_handle(lbm_handle *h);
 
+// Launch one step of a handle's own kernels on stream s from state `src`
+// (lattice, or AA phase), plane statistics fused when `stats`.
+int lbm_launch_step(lbm_handle *h, cudaStream_t s, int src, bool stats);
+
 // Record an error message for lbm_last_error() and return `code`.
 int lbm_record_error(int code, const char *msg);
+
+// Host-side NVTX range over one library call (visible in Nsight timelines; a
+// no-op without a profiler attached).
+struct LbmRange {
+    explicit LbmRange(const char *name) { nvtxRangePushA(name); }
+    ~LbmRange() { nvtxRangePop(); }
+    LbmRange(const LbmRange &) = delete;
+    LbmRange &operator=(const LbmRange &) = delete;
+};

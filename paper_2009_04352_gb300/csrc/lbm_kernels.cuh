@@ -15,28 +15,38 @@ namespace lbm {
 //   fb*_a = fb_a + omega (f^eq_a - w_a - fb_a) + F_a,  omega = 1 / tau_eff
 //   f^eq_a - w_a = w_a [drho + rho (3 e.u + 9/2 (e.u)^2 - 3/2 u.u)]
 //   F_a = (1 - omega / 2) w_a [3 (e_a - u) . F + 9 (e_a . u)(e_a . F)]
-// The update delta_a = fb*_a - fb_a is formed per opposite pair from its even
-// and odd parts. In exact arithmetic sum delta = 0 and sum e delta = F; in
-// FP32 the rounded weights w_a break the lattice isotropy by ~1e-8, which
-// biases the momentum of every cell by ~1e-8 rho u per step, a sizeable
-// fraction of a body force of 1e-7. The odd parts are therefore corrected on
-// the axis pairs so that sum e delta = F, and the rest population takes
-// -sum of the others, so mass and momentum are exact up to the final store.
+// The update is formed per opposite pair from its even and odd parts. In
+// exact arithmetic sum delta = 0 and sum e delta = F. FP32 roundings that
+// repeat the same way in every cell add up over the channel to a momentum
+// error of the order of a percent of the channels' body force (~1e-8 of
+// rho u per step against F ~ 4e-8): the rounded weights 1/18 and 1/36 break
+// the lattice sums, and the small half force added to j rounds to whole ulps
+// of j alike everywhere. Here the weights are scaled by 36 (36 w = 12, 2, 1:
+// exact) with 1/36 folded into the rate, the non-equilibrium difference is
+// formed before the rate multiplies it, and the odd (momentum) part uses
+// rho (e.u) = e.(j + F/2) directly. The axis pairs then take the small
+// momentum residual, so sum e delta = F exactly up to the final store, and
+// the rest population its own update (mass change zero up to unbiased
+// roundings). The FP16-storage form of the packed kernels (lbm_pair.cuh)
+// keeps rounded weights with the rate folded in and corrects mass and
+// momentum on the rest population and the axis pairs.
 struct CellState {
     float rho, ux, uy, uz;
 };
 
-// u = (j + F/2) / rho evaluated as jF + jF (1/rho - 1) with 1/rho - 1 =
-// -drho / rho, which avoids the systematic rounding of 1/rho near 1.
+// u = (j + F/2) / rho evaluated as j + (j (1/rho - 1) + (F/2) / rho) with
+// 1/rho - 1 = -drho / rho: no rounded 1/rho near 1, and the half force, a few
+// ulps of j in the channels, is added to a value that varies from cell to
+// cell rather than straight to j, whose rounding would move it to whole ulps
+// of j the same way everywhere.
 __device__ __forceinline__ CellState velocity(const Moments &m, const Phys &p)
 {
     CellState c;
     c.rho = 1.f + m.drho;
     const float idev = -m.drho / c.rho;
-    const float jx = __fmaf_rn(0.5f, p.Fx, m.jx), jy = __fmaf_rn(0.5f, p.Fy, m.jy), jz = __fmaf_rn(0.5f, p.Fz, m.jz);
-    c.ux = fmaf(jx, idev, jx);
-    c.uy = fmaf(jy, idev, jy);
-    c.uz = fmaf(jz, idev, jz);
+    c.ux = m.jx + fmaf(m.jx, idev, fmaf(p.hF[0], idev, p.hF[0]));
+    c.uy = m.jy + fmaf(m.jy, idev, fmaf(p.hF[1], idev, p.hF[1]));
+    c.uz = m.jz + fmaf(m.jz, idev, fmaf(p.hF[2], idev, p.hF[2]));
     return c;
 }
 
@@ -117,33 +127,39 @@ __device__ __forceinline__ CellState collide(const float (&f)[Q], float (&fs)[Q]
         fs[0] = f[0] - mass;
         return c;
     }
-    const float uF = ux * p.Fx + uy * p.Fy + uz * p.Fz;
-    const float S0 = m.drho - 1.5f * rho * usq;   // isotropic part of (f^eq - w) / w
-    const float r45 = 4.5f * rho, r3 = 3.f * rho;
-    const float g9 = 9.f * gk, g3 = 3.f * gk;
-
+    // BGK (see the comment above the struct): weights scaled by 36, o36 = omega / 36
+    const float uF = fmaf(ux, p.Fx, fmaf(uy, p.Fy, uz * p.Fz));
+    const float S0 = fmaf(-1.5f, rho * usq, m.drho);   // isotropic part of (f^eq - w) / w
+    const float o36 = omega * (1.f / 36.f);
+    const float r45 = 4.5f * rho;
+    const float g9 = 0.25f * gk, g3 = (1.f / 12.f) * gk;   // 9 gk / 36, 3 gk / 36
+    const float mgu = (-1.f / 12.f) * gk * uF;              // -3 gk u.F / 36
+    fs[0] = f[0] + fmaf(o36, fmaf(-36.f, f[0], 12.f * S0), 12.f * mgu);
     float de[9], dd[9];
-    float mass = 0.f, mx = 0.f, my = 0.f, mz = 0.f;
+    float mx = 0.f, my = 0.f, mz = 0.f;
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
         const int a = 2 * k + 1;
-        const float w = (float)w_of(a);
+        const float W = k < 3 ? 2.f : 1.f;   // 36 w
         const float eu = ex_of(a) * ux + ey_of(a) * uy + ez_of(a) * uz;
-        const float eF = ex_of(a) * p.Fx + ey_of(a) * p.Fy + ez_of(a) * p.Fz;
+        const float ej = ex_of(a) * m.jx + ey_of(a) * m.jy + ez_of(a) * m.jz;
+        const float WeF = p.WeF[k];
         const float fe = 0.5f * (f[a] + f[a + 1]);
         const float fo = 0.5f * (f[a] - f[a + 1]);
-        de[k] = omega * (w * (S0 + r45 * eu * eu) - fe) + w * (g9 * eu * eF - g3 * uF);
-        dd[k] = omega * (w * (r3 * eu) - fo) + w * (g3 * eF);
-        mass += de[k];
+        // 36 (f^eq - f) of the pair's even and odd parts, rho (e.u) = e.(j + F/2)
+        const float ne = fmaf(W * r45 * eu, eu, fmaf(-36.f, fe, W * S0));
+        const float nd = fmaf(3.f * W, ej, fmaf(-36.f, fo, 1.5f * WeF));
+        de[k] = fmaf(o36, ne, fmaf(g9 * WeF, eu, W * mgu));
+        dd[k] = fmaf(o36, nd, g3 * WeF);
         if (ex_of(a)) mx += ex_of(a) * dd[k];
         if (ey_of(a)) my += ey_of(a) * dd[k];
         if (ez_of(a)) mz += ez_of(a) * dd[k];
     }
-    // pairs 0, 1, 2 are the axis directions 1, 3, 5 (e = unit x, y, z)
+    // pairs 0, 1, 2 are the axis directions 1, 3, 5: they take the momentum
+    // residual, so that sum e delta = F exactly up to the final store
     dd[0] += 0.5f * p.Fx - mx;
     dd[1] += 0.5f * p.Fy - my;
     dd[2] += 0.5f * p.Fz - mz;
-    fs[0] = f[0] - 2.f * mass;
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
         const int a = 2 * k + 1;

@@ -220,12 +220,13 @@ __device__ __forceinline__ void wall_layer_pair(float2 (&f)[Q], const PairState 
 // s_k = f_a + f_b and d_k = f_a - f_b carry all moments the update needs,
 //   drho = f_0 + sum s,  j = sum e_k d_k,  Pi_ab = sum e_k,a e_k,b s_k,
 // and the update of the pair is  delta_a = de + dd,  delta_b = de - dd  with
-//   de = omega w (S0 + 9/2 rho (e.u)^2) - 3 w gk u.F + 9 w gk (e.u)(e.F) - omega s / 2
-//   dd = 3 omega w rho (e.u) + 3 w gk (e.F) - omega d / 2.
+//   de = omega (w (S0 + 9/2 rho (e.u)^2) - s / 2) - 3 w gk u.F + 9 w gk (e.u)(e.F)
+//   dd = omega (3 w rho (e.u) - d / 2) + 3 w gk (e.F),
+// evaluated with the weights scaled by 36 as collide() states.
 // Only the half sums and differences s/2, d/2 are kept through the collision
 // (the new populations are their sum and difference), which keeps 18 fewer
 // values live.
-template <int COLL = COLL_BGK>
+template <int COLL = COLL_BGK, bool EXACT_W = false>
 __device__ __forceinline__ PairState collide_pair(float2 (&f)[Q], const Phys &p, float smag)
 {
     PairState c;
@@ -261,10 +262,19 @@ __device__ __forceinline__ PairState collide_pair(float2 (&f)[Q], const Phys &p,
 
     c.rho = add2(bc(1.f), drho);
     const float2 idev = make_float2(-drho.x / c.rho.x, -drho.y / c.rho.y);   // 1/rho - 1
-    const float2 jfx = add2(jx, bc(p.hF[0])), jfy = add2(jy, bc(p.hF[1])), jfz = add2(jz, bc(p.hF[2]));
-    c.ux = fma2(jfx, idev, jfx);
-    c.uy = fma2(jfy, idev, jfy);
-    c.uz = fma2(jfz, idev, jfz);
+    if constexpr (EXACT_W) {
+        // u = j + (j (1/rho - 1) + F/2 / rho), as velocity() in lbm_kernels.cuh
+        c.ux = add2(jx, fma2(jx, idev, fma2(bc(p.hF[0]), idev, bc(p.hF[0]))));
+        c.uy = add2(jy, fma2(jy, idev, fma2(bc(p.hF[1]), idev, bc(p.hF[1]))));
+        c.uz = add2(jz, fma2(jz, idev, fma2(bc(p.hF[2]), idev, bc(p.hF[2]))));
+    } else {
+        // u = (j + F/2)(1 + (1/rho - 1)); the momentum projection of the
+        // update below makes its momentum exact whatever the rounding of u
+        const float2 jfx = add2(jx, bc(p.hF[0])), jfy = add2(jy, bc(p.hF[1])), jfz = add2(jz, bc(p.hF[2]));
+        c.ux = fma2(jfx, idev, jfx);
+        c.uy = fma2(jfy, idev, jfy);
+        c.uz = fma2(jfz, idev, jfz);
+    }
     const float2 rho = c.rho, ux = c.ux, uy = c.uy, uz = c.uz;
 
     const float2 cd = mul2(drho, bc(1.f / 3.f));
@@ -382,7 +392,73 @@ __device__ __forceinline__ PairState collide_pair(float2 (&f)[Q], const Phys &p,
             f[2 * k + 2] = sub2(hs[k], hd[k]);
         }
         return c;
+    } else if constexpr (EXACT_W) {
+    // BGK with the weights scaled by 36 (36 w = 12 rest, 2 axis, 1 diagonal:
+    // exact) and 1/36 folded into the rate, o36 = omega / 36. Per pair, with
+    // W = 36 w, the non-equilibrium difference is formed before the rate
+    // multiplies it, and the odd part uses rho (e.u) = e.(j + F/2) directly:
+    //   ne = 36 (feq_even - hs) = W (S0 + 9/2 rho (e.u)^2) - 36 hs
+    //   nd = 36 (feq_odd - hd)  = 3 W (e.j) + 3 W (e.F) / 2 - 36 hd
+    //   de = o36 ne + W gk (9 (e.u)(e.F) - 3 u.F) / 36,  dd = o36 nd + W gk 3 (e.F) / 36
+    // and the rest population its own update 36 (feq_0 - f_0) = 12 S0 - 36 f_0.
+    // The axis pairs take the momentum residual F/2 - sum e dd (zero in exact
+    // arithmetic): it now holds only the roundings of small non-equilibrium
+    // terms, not the rounding of the weights or of the rate times the
+    // equilibrium, which halves the update's FP32 error against an FP64
+    // reference while momentum stays exact up to the final store; the mass
+    // change is zero up to unbiased roundings.
+    const float2 gk = fma2(bc(-0.5f), omega, bc(1.f));
+    const float2 o36 = mul2(omega, bc(1.f / 36.f));
+    const float2 usq = fma2(ux, ux, fma2(uy, uy, mul2(uz, uz)));
+    const float2 uF = fma2(ux, bc(p.Fx), fma2(uy, bc(p.Fy), mul2(uz, bc(p.Fz))));
+    const float2 S0 = fma2(bc(-1.5f), mul2(rho, usq), drho);
+    const float2 r45 = mul2(bc(4.5f), rho);
+    const float2 r45a = add2(r45, r45), S0a = add2(S0, S0);               // W = 2 (exact doublings)
+    const float2 g9 = mul2(bc(0.25f), gk);                                 // 9 gk / 36
+    const float2 g3 = mul2(bc(1.f / 12.f), gk);                            // 3 gk / 36
+    const float2 mgu = mul2(mul2(bc(-1.f / 12.f), gk), uF);                // -3 gk u.F / 36
+    const float2 mgua = add2(mgu, mgu);
+
+    // e.u and e.j of the odd member of each pair (directions 1, 3, ..., 17)
+    const float2 eus[9] = {ux, uy, uz, add2(ux, uy), add2(ux, uz), add2(uy, uz),
+                           sub2(ux, uy), sub2(ux, uz), sub2(uy, uz)};
+    const float2 ejs[9] = {jx, jy, jz, add2(jx, jy), add2(jx, jz), add2(jy, jz),
+                           sub2(jx, jy), sub2(jx, jz), sub2(jy, jz)};
+    f[0] = add2(f[0], fma2(o36, fma2(bc(-36.f), f[0], mul2(bc(12.f), S0)), mul2(bc(12.f), mgu)));
+    float2 mx, my, mz;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const int a = 2 * k + 1;
+        const bool axis = k < 3;
+        const float W3 = axis ? 6.f : 3.f;    // 3 W
+        const float2 eu = eus[k];
+        const float2 WeF = bc(p.WeF[k]);      // 36 w (e.F)
+        const float2 ne = fma2(mul2(axis ? r45a : r45, eu), eu, fma2(bc(-36.f), hs[k], axis ? S0a : S0));
+        const float2 nd = fma2(bc(W3), ejs[k], fma2(bc(-36.f), hd[k], mul2(bc(1.5f), WeF)));
+        const float2 de = fma2(o36, ne, fma2(mul2(g9, WeF), eu, axis ? mgua : mgu));
+        const float2 dd = fma2(o36, nd, mul2(g3, WeF));
+        if (k == 0) mx = dd;
+        else if (ex_of(a)) mx = ex_of(a) > 0 ? add2(mx, dd) : sub2(mx, dd);
+        if (k == 1) my = dd;
+        else if (k > 1 && ey_of(a)) my = ey_of(a) > 0 ? add2(my, dd) : sub2(my, dd);
+        if (k == 2) mz = dd;
+        else if (k > 2 && ez_of(a)) mz = ez_of(a) > 0 ? add2(mz, dd) : sub2(mz, dd);
+        hs[k] = add2(hs[k], de);
+        hd[k] = add2(hd[k], dd);
+    }
+    hd[0] = add2(hd[0], sub2(bc(p.hF[0]), mx));
+    hd[1] = add2(hd[1], sub2(bc(p.hF[1]), my));
+    hd[2] = add2(hd[2], sub2(bc(p.hF[2]), mz));
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        f[2 * k + 1] = add2(hs[k], hd[k]);
+        f[2 * k + 2] = sub2(hs[k], hd[k]);
+    }
+    return c;
     } else {
+    // BGK with rounded weights folded into the rate; the momentum and mass
+    // of the update are then corrected on the axis pairs and the rest
+    // population (the storage form of FP16, whose rounding dominates)
     const float2 gk = fma2(bc(-0.5f), omega, bc(1.f));
     const float2 nw = mul2(bc(-1.f), omega);                               // -omega
     const float2 usq = fma2(ux, ux, fma2(uy, uy, mul2(uz, uz)));
@@ -510,7 +586,7 @@ __device__ __forceinline__ void pair_tile(const T *src, T *dst, const Geom &g, c
             *t = make_float4(twx.x, twz.x, twx.y, twz.y);
         }
     } else {
-        c = collide_pair<COLL>(f, p, row_smag(p, y, g.ny));
+        c = collide_pair<COLL, sizeof(T) == 4>(f, p, row_smag(p, y, g.ny));
     }
 
     if (ROWS != ROWS_INTERIOR && !node_row && (y == 0 || y == g.ny - 1)) {
@@ -581,6 +657,24 @@ __global__ void __launch_bounds__(128, LBM_PAIR_MIN_BLOCKS) k_step_pair(const T 
     const int y = blockIdx.y, z = blockIdx.z;
     const long long blk = ((long long)y * g.nz + z) * gridDim.x + blockIdx.x;
     pair_tile<T, STATS, COLL>(src, dst, g, p, tw_out, STATS ? part + blk * K_PART : nullptr, blockIdx.x, y, z);
+}
+
+// The two wall rows of the four-cell (FP16) step, run with the two-cell tile:
+// a CTA of twice the four-cell launch's threads covers the same cells as one
+// four-cell CTA (so the partial sums keep the four-cell layout) and each
+// thread carries half the serial work (wall law, collision) of a four-cell
+// thread, which shortens this one-wave, latency-bound launch. The two tile
+// forms compute the same bits. grid (four-cell tiles per row, 2, nz); LAY as
+// in pair_tile (for the AA kinds src == dst).
+template <typename T, bool STATS, int COLL, int LAY = LAY_PULL>
+__global__ void __launch_bounds__(256) k_step_pair_wall(const T *src, T *dst, Geom g, Phys p,
+                                                        float *__restrict__ tw_out, double *__restrict__ part)
+{
+    pdl_begin();
+    const int y = blockIdx.y == 0 ? 0 : g.ny - 1, z = blockIdx.z;
+    const long long blk = ((long long)y * g.nz + z) * gridDim.x + blockIdx.x;
+    pair_tile<T, STATS, COLL, LAY, ROWS_WALL>(src, dst, g, p, tw_out, STATS ? part + blk * K_PART : nullptr,
+                                              blockIdx.x, y, z);
 }
 
 // The two-cell step on the single AA array (LAY_AA_EVEN or LAY_AA_ODD).

@@ -258,9 +258,9 @@ __device__ __forceinline__ void quad_tile(const __half *src, __half *dst, const 
         t[1] = twb;
     }
     if (LAY == LAY_AA_ODD) {
-        if (y == 0)
+        if (ROWS != ROWS_INTERIOR && y == 0)
             push_quad<ROW_BOTTOM>(dst, g, p.wall, xl, y, z, zm, zp, lane, valid, r);
-        else if (y == g.ny - 1)
+        else if (ROWS != ROWS_INTERIOR && y == g.ny - 1)
             push_quad<ROW_TOP>(dst, g, p.wall, xl, y, z, zm, zp, lane, valid, r);
         else
             push_quad<ROW_INTERIOR>(dst, g, p.wall, xl, y, z, zm, zp, lane, valid, r);
@@ -292,16 +292,18 @@ __global__ void __launch_bounds__(128, LBM_QUAD_MIN_BLOCKS) k_step_quad(const __
                                            blockIdx.x, y, z);
 }
 
-// The four-cell step on the single AA array (LAY_AA_EVEN or LAY_AA_ODD).
-template <bool STATS, int COLL, int LAY>
+// The four-cell step on the single AA array (LAY_AA_EVEN or LAY_AA_ODD) over
+// the row set ROWS (grid.y ny, or ny - 2 for the interior rows, row
+// blockIdx.y + 1).
+template <bool STATS, int COLL, int LAY, int ROWS = ROWS_ALL>
 __global__ void __launch_bounds__(128, LBM_QUAD_MIN_BLOCKS) k_step_quad_aa(__half *f, Geom g, Phys p,
                                                                             float *__restrict__ tw_out,
                                                                             double *__restrict__ part)
 {
     pdl_begin();
-    const int y = blockIdx.y, z = blockIdx.z;
+    const int y = ROWS == ROWS_INTERIOR ? (int)blockIdx.y + 1 : (int)blockIdx.y, z = blockIdx.z;
     const long long blk = ((long long)y * g.nz + z) * gridDim.x + blockIdx.x;
-    quad_tile<STATS, COLL, LAY>(f, f, g, p, tw_out, STATS ? part + blk * K_PART : nullptr, blockIdx.x, y, z);
+    quad_tile<STATS, COLL, LAY, ROWS>(f, f, g, p, tw_out, STATS ? part + blk * K_PART : nullptr, blockIdx.x, y, z);
 }
 
 }  // namespace lbm

@@ -11,16 +11,18 @@
 // the stage's "empty" mbarrier so that warp 0 can refill it. Rows are whole, so
 // every byte copied is used exactly once. The copies of the next S-1 rows are
 // in flight while the CTA computes the current one, so DRAM latency is covered
-// by the ring rather than by occupancy. Every wait on an mbarrier is bounded:
-// on timeout the warp sets the error flag; warp 0 also waits (bounded) for the
-// copies it still has in flight before returning.
+// by the ring rather than by occupancy. Every wait on an mbarrier is bounded
+// by the launch's wait limit: on timeout the warp sets the error flag; warp 0
+// also waits for the copies it still has in flight before returning, bounded
+// by the fixed WAIT_CYCLES whatever the launch's limit, so that no copy can
+// land in shared memory after its CTA has exited.
 #pragma once
 
 #include "lbm_pair.cuh"
 
 namespace lbm {
 
-constexpr long long WAIT_CYCLES = 1LL << 32;   // ~2 s at 2 GHz
+constexpr long long WAIT_CYCLES = 1LL << 32;   // ~2 s at 2 GHz: default limit, and the drain limit
 constexpr int ROW_MAX_STAGES = 4;
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -35,12 +37,15 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t byt
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
+// Non-blocking test of phase `parity` (test_wait returns at once; try_wait
+// may suspend the thread for a hardware-chosen time, which would let a short
+// wait limit pass unnoticed).
 __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity)
 {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
         : "r"(bar), "r"(parity)
@@ -55,15 +60,18 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_
                  : "memory");
 }
 
-// Warp-uniform bounded wait for phase `parity` of the barrier.
-__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity)
+// Warp-uniform wait for phase `parity` of the barrier, given up after `limit`
+// clock cycles (returns false). Polls with a short sleep between tests, so a
+// waiting warp takes few issue slots from the warps that compute.
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, long long limit)
 {
     if (__all_sync(0xffffffffu, mbar_test(bar, parity))) return true;
     const long long t0 = clock64();
     for (;;) {
-        if (__all_sync(0xffffffffu, mbar_test(bar, parity))) return true;
         const long long dt = __shfl_sync(0xffffffffu, clock64() - t0, 0);
-        if (dt > WAIT_CYCLES) return false;
+        if (dt > limit) return false;
+        __nanosleep(20);
+        if (__all_sync(0xffffffffu, mbar_test(bar, parity))) return true;
     }
 }
 
@@ -136,7 +144,7 @@ __device__ __forceinline__ void read_rows(const T *stage, int nx, int wall, int 
 template <typename T, bool STATS, int NW, int COLL = COLL_BGK>
 __global__ void __launch_bounds__(NW * 32, 16 / NW) k_step_rows(const T *__restrict__ src, T *__restrict__ dst, Geom g, Phys p,
                                                       float *__restrict__ tw_out, double *__restrict__ part,
-                                                      int *__restrict__ err, int S)
+                                                      int *__restrict__ err, int S, long long wait_limit)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -176,21 +184,22 @@ __global__ void __launch_bounds__(NW * 32, 16 / NW) k_step_rows(const T *__restr
             const long long ahead = i + S - 1;
             if (ahead < mine) {
                 const int st = (int)(ahead % S);
-                if (ahead >= S && !warp_wait(smem_addr(empty + st), (uint32_t)(((ahead / S) - 1) & 1))) {
+                if (ahead >= S && !warp_wait(smem_addr(empty + st), (uint32_t)(((ahead / S) - 1) & 1), wait_limit)) {
                     if (lane == 0) atomicExch(err, 1);
                     for (long long k = i; k < ahead; ++k)   // copies still in flight
-                        warp_wait(smem_addr(full + k % S), (uint32_t)((k / S) & 1));
+                        warp_wait(smem_addr(full + k % S), (uint32_t)((k / S) & 1), WAIT_CYCLES);
                     return;
                 }
                 issue(ahead);
             }
         }
         const int st = (int)(i % S);
-        if (!warp_wait(smem_addr(full + st), (uint32_t)((i / S) & 1))) {
+        if (!warp_wait(smem_addr(full + st), (uint32_t)((i / S) & 1), wait_limit)) {
             if (lane == 0) atomicExch(err, 1);
             if (warp == 0) {
                 const long long last = (i + S - 1 < mine ? i + S - 1 : mine - 1);
-                for (long long k = i; k <= last; ++k) warp_wait(smem_addr(full + k % S), (uint32_t)((k / S) & 1));
+                for (long long k = i; k <= last; ++k)
+                    warp_wait(smem_addr(full + k % S), (uint32_t)((k / S) & 1), WAIT_CYCLES);
             }
             return;
         }
@@ -206,7 +215,7 @@ __global__ void __launch_bounds__(NW * 32, 16 / NW) k_step_rows(const T *__restr
         for (int x0 = 2 * (warp * 32 + lane); x0 < g.nx; x0 += 64 * NW) {
             float2 f[Q];
             read_rows<T>(stage, g.nx, p.wall, y, g.ny, x0, f);
-            const PairState c = collide_pair<COLL>(f, p, row_smag(p, y, g.ny));
+            const PairState c = collide_pair<COLL, sizeof(T) == 4>(f, p, row_smag(p, y, g.ny));
             float2 twx = bc(0.f), twz = bc(0.f);
             if (wall_row) {
                 float fa[Q], fb[Q];

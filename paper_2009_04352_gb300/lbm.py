@@ -33,6 +33,7 @@ COLLISION_BGK, COLLISION_MRT = 0, 1
 LAW_SPALDING, LAW_LOG, LAW_POWER = 0, 1, 2
 FP32, FP16_SHIFTED = 0, 1
 PULL2, AA = 0, 1
+BATCH_PERSISTENT, BATCH_MEMBER_GRIDS = 1, 2
 
 
 class LbmError(RuntimeError):
@@ -83,6 +84,7 @@ _SIGNATURES = {
     "lbm_conservation": (C.c_int, [_VP, _DP]),
     "lbm_plane_profile_noalloc": (C.c_int, [_VP, _VP]),
     "lbm_sync": (C.c_int, [_VP]),
+    "lbm_set_wait_limit": (C.c_int, [_VP, C.c_longlong]),
     "lbm_batch_create": (C.c_int, [C.c_int, C.POINTER(lbm_member), C.c_int, _VP, C.POINTER(_VP)]),
     "lbm_batch_member": (_VP, [_VP, C.c_int]),
     "lbm_batch_cells": (C.c_longlong, [_VP]),
@@ -91,6 +93,8 @@ _SIGNATURES = {
     "lbm_batch_set_config": (C.c_int, [_VP, C.c_int, C.c_int]),
     "lbm_batch_get_config": (C.c_int, [_VP, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                        C.POINTER(C.c_longlong)]),
+    "lbm_batch_set_form": (C.c_int, [_VP, C.c_int, C.c_int]),
+    "lbm_batch_get_form": (C.c_int, [_VP, C.POINTER(C.c_int)]),
     "lbm_batch_autotune": (C.c_int, [_VP, C.c_int, _DP]),
     "lbm_batch_set_les": (C.c_int, [_VP, C.c_int, _DP, C.c_double]),
     "lbm_batch_sync": (C.c_int, [_VP]),
@@ -240,6 +244,10 @@ def lbm_sync(h):
     _check(lib().lbm_sync(h))
 
 
+def lbm_set_wait_limit(h, cycles):
+    _check(lib().lbm_set_wait_limit(h, int(cycles)))
+
+
 def lbm_destroy(h):
     lib().lbm_destroy(h)
 
@@ -359,6 +367,9 @@ class Channel:
     def sync(self):
         lbm_sync(self._h)
 
+    def set_wait_limit(self, cycles):
+        lbm_set_wait_limit(self._h, cycles)
+
 
 # ------------------------------------------------------------ batched ensemble
 
@@ -421,7 +432,17 @@ class Batch:
     def config(self):
         t, c, g, tl = C.c_int(), C.c_int(), C.c_int(), C.c_longlong()
         _check(lib().lbm_batch_get_config(self._b, C.byref(t), C.byref(c), C.byref(g), C.byref(tl)))
-        return {"threads": t.value, "ctas_per_sm": c.value, "grid": g.value, "tiles": tl.value}
+        st = C.c_int()
+        form = int(lib().lbm_batch_get_form(self._b, C.byref(st)))
+        return {"threads": t.value, "ctas_per_sm": c.value, "grid": g.value, "tiles": tl.value,
+                "form": form, "streams": st.value}
+
+    def set_form(self, form, streams=0):
+        _check(lib().lbm_batch_set_form(self._b, int(form), int(streams)))
+
+    @property
+    def form(self):
+        return int(lib().lbm_batch_get_form(self._b, None))
 
     def set_les(self, collision=COLLISION_BGK, u_tau_ref=None, a_plus=0.0):
         ut = None if u_tau_ref is None else np.ascontiguousarray(np.asarray(u_tau_ref, dtype=np.float64))
