@@ -57,7 +57,13 @@ def test_invalid_arguments_rejected_without_device():
            dict(nx=8, ny=8, nz=8, tau=0.6, layout=3),
            dict(nx=1 << 16, ny=1 << 10, nz=1 << 10, tau=0.6),  # > 2^31 cells
            dict(nx=8, ny=8, nz=8, tau=0.6, law=3),     # unknown wall law
-           dict(nx=8, ny=8, nz=8, tau=0.6, law=lbm.LAW_LOG, B=0.2)]  # log branches never cross
+           dict(nx=8, ny=8, nz=8, tau=0.6, law=lbm.LAW_LOG, B=0.2),  # log branches never cross
+           # corrupted configurations: NaN relaxation time or Smagorinsky
+           # constant, non-finite body force
+           dict(nx=8, ny=8, nz=8, tau=float("nan")),
+           dict(nx=8, ny=8, nz=8, tau=0.6, cs=float("nan")),
+           dict(nx=8, ny=8, nz=8, tau=0.6, force=(float("inf"), 0, 0)),
+           dict(nx=8, ny=8, nz=8, tau=0.6, force=(0, float("nan"), 0))]
     for kw in bad:
         kw = dict(kw)
         args = dict(cs=0.1, force=(1e-6, 0, 0), wall=lbm.WALL_WFB, precision=lbm.FP32, layout=lbm.PULL2,
@@ -76,6 +82,7 @@ def test_null_handle_calls_fail_cleanly():
     L = lbm.lib()
     assert L.lbm_step(None, 1) == lbm.LBM_ERR_ARG
     assert L.lbm_sync(None) == lbm.LBM_ERR_ARG
+    assert L.lbm_set_wait_limit(None, 1) == lbm.LBM_ERR_ARG
     assert L.lbm_get_step(None) == -1
     L.lbm_destroy(None)
 
@@ -113,6 +120,7 @@ def test_bench_launch_and_kernel_bookkeeping():
     assert bench.launches_per_step(c2, lbm.FP32) == 1
     assert bench.launches_per_step(c3, lbm.FP16_SHIFTED) == 2           # interior + wall rows
     assert bench.launches_per_step(c3, lbm.FP16_SHIFTED, lbm.AA) == 1
+    assert bench.launches_per_step(c3, lbm.FP16_SHIFTED, mrt=True) == 1
     assert bench.launches_per_step(c3.with_(ny=2), lbm.FP16_SHIFTED) == 1
     assert bench.headline_kernel(c2, lbm.FP32) == "k_step_pair"
     assert bench.headline_kernel(c3, lbm.FP16_SHIFTED) == "k_step_quad"

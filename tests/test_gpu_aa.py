@@ -12,10 +12,10 @@ import pytest
 
 import oracle
 from paper_2009_04352_gb300 import lbm, workload
+from parity import check_state, floors, reference
 
 pytestmark = pytest.mark.gpu
 
-TOL = {lbm.FP32: 1e-5, lbm.FP16_SHIFTED: 5e-3}
 SMALL = workload.CASES["c1"]
 WALLS = [workload.WALL_BB, workload.WALL_WFB, workload.WALL_FREESLIP]
 # ragged rows, rows shorter than a warp, one pair or one quad per row, ny = 2
@@ -95,18 +95,16 @@ def test_aa_equals_pull_ragged(case, wall, precision):
 @pytest.mark.parametrize("precision", [lbm.FP32, lbm.FP16_SHIFTED])
 def test_aa_parity_with_oracle_100_steps(precision):
     case = SMALL
-    L = oracle.Lattice.from_case(case)
-    L.init_channel(workload.u_mean_profile(case), workload.noise_amplitude(case), case.seed)
-    L.step(99)                         # an odd count: the AA state is in phase 1
-    _, u_ref = L.moments()
-    tw_ref = L.wall_stress()
-    L.close()
+    checkpoints = (98, 99)             # both phases; an odd count leaves the AA state in phase 1
+    ref = reference(case, checkpoints, workload.WALL_WFB)
+    fl = floors(case, checkpoints, precision, workload.WALL_WFB)
     ch = lbm.Channel.from_case(case, precision=precision, layout=lbm.AA)
     ch.init_channel(workload.u_mean_profile(case), workload.noise_amplitude(case), case.seed)
-    ch.step(99)
-    _, u = ch.moments()
-    assert np.max(np.abs(u - u_ref)) <= TOL[precision] * np.max(np.abs(u_ref))
-    assert np.max(np.abs(ch.wall_stress() - tw_ref)) <= 10 * TOL[precision] * np.max(np.abs(tw_ref))
+    t = 0
+    for c in checkpoints:
+        ch.step(c - t)
+        t = c
+        check_state(ch, ref[c], fl[c], precision, workload.WALL_WFB, populations=True, tag=c)
     ch.close()
 
 

@@ -1,16 +1,14 @@
 """MRT collision and van Driest damping on the GPU against the oracle (the
 paper's LES operator of Sec. 3.1: MRT, standard Smagorinsky, van Driest)."""
-import functools
-
 import numpy as np
 import pytest
 
 import oracle
 from paper_2009_04352_gb300 import lbm, workload
+from parity import check_state, floors, reference
 
 pytestmark = pytest.mark.gpu
 
-TOL = {lbm.FP32: 1e-5, lbm.FP16_SHIFTED: 5e-3}
 SMALL = workload.CASES["c1"]
 A_PLUS = 26.0
 
@@ -25,18 +23,6 @@ def _cuda():
     oracle.build()
 
 
-@functools.lru_cache(maxsize=None)
-def oracle_u(case, wall, steps, damping):
-    L = oracle.Lattice.from_case(case, wall=wall)
-    L.set_les(1, case.u_tau if damping else 0.0, A_PLUS if damping else 0.0)
-    L.init_channel(workload.u_mean_profile(case), workload.noise_amplitude(case), case.seed)
-    L.step(steps)
-    _, u = L.moments()
-    tw = L.wall_stress()
-    L.close()
-    return u, tw
-
-
 def rel(a, b):
     return float(np.max(np.abs(np.asarray(a, dtype=np.float64) - b)) / np.max(np.abs(b)))
 
@@ -49,15 +35,15 @@ def test_mrt_parity_100_steps(wall, precision, kernel, damping):
     if kernel == lbm.KERNEL_QUAD and precision != lbm.FP16_SHIFTED:
         pytest.skip("the four-cell kernel serves FP16 storage only")
     case = SMALL
-    u_ref, tw_ref = oracle_u(case, wall, 100, damping)
+    les = (lbm.COLLISION_MRT, case.u_tau if damping else 0.0, A_PLUS if damping else 0.0)
+    ref = reference(case, (100,), wall, les)[100]
+    fl = floors(case, (100,), precision, wall, les)[100]
     ch = lbm.Channel.from_case(case, precision=precision, wall=wall)
     ch.set_kernel(kernel)
-    ch.set_les(lbm.COLLISION_MRT, case.u_tau if damping else 0.0, A_PLUS if damping else 0.0)
+    ch.set_les(*les)
     ch.init_channel(workload.u_mean_profile(case), workload.noise_amplitude(case), case.seed)
     ch.step(100)
-    _, u = ch.moments()
-    assert rel(u, u_ref) <= TOL[precision]
-    assert rel(ch.wall_stress(), tw_ref) <= 10 * TOL[precision]
+    check_state(ch, ref, fl, precision, wall, populations=True, tag=kernel)
     ch.close()
 
 

@@ -1,27 +1,22 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
 same seeded inputs.
 
-Bounds (relative L_inf, max |gpu - oracle| / max |oracle| over cells and
-components): 1e-5 for FP32 storage and 5e-3 for FP16-shifted storage, on the
-velocity u and on the population deviations f - w. The density deviation
-rho - 1 is about 1% of the population deviations it is summed from, so the
-once-per-step rounding of 19 stored deviations puts its relative error about
-100 times higher (about 2e-5 per step for FP32, growing as a random walk): the
-bound for rho - 1 is 3e-4 (FP32) and 5e-2 (FP16) over 100 steps."""
-import functools
-
+Relative L_inf (max |gpu - oracle| / max |oracle| over cells and components)
+of the velocity u, the density deviation rho - 1, the population deviations
+f - w and the wall stress, bounded by the benchmark's tolerance (1e-5 FP32, 5e-3
+FP16 storage) or by twice the measured storage-rounding floor, whichever is
+larger (tests/parity.py states the bounds and how the floor is measured)."""
 import numpy as np
 import pytest
 
 import oracle
 from paper_2009_04352_gb300 import lbm, workload
+from parity import W, check_state, floors, reference, rel
 
 pytestmark = pytest.mark.gpu
 
-TOL = {lbm.FP32: 1e-5, lbm.FP16_SHIFTED: 5e-3}
-TOL_RHO = {lbm.FP32: 3e-4, lbm.FP16_SHIFTED: 5e-2}
 WALLS = [workload.WALL_BB, workload.WALL_WFB, workload.WALL_FREESLIP]
-_W = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+rel_linf = rel
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -34,26 +29,9 @@ def _cuda():
     oracle.build()
 
 
-def rel_linf(got, ref):
-    scale = np.max(np.abs(ref))
-    return float(np.max(np.abs(np.asarray(got, dtype=np.float64) - ref)) / max(scale, 1e-300))
-
-
-@functools.lru_cache(maxsize=None)
 def oracle_run(case, wall, checkpoints, stats_every=0):
     """Moments, wall stress and populations of the oracle at each checkpoint."""
-    L = oracle.Lattice.from_case(case, stats_every=stats_every, wall=wall)
-    L.init_channel(workload.u_mean_profile(case), workload.noise_amplitude(case), case.seed)
-    out = {}
-    t = 0
-    for c in checkpoints:
-        L.step(c - t)
-        t = c
-        rho, u = L.moments()
-        out[c] = dict(rho=rho, u=u, tw=L.wall_stress(), f=L.populations(), cons=L.conservation(),
-                      stats=L.plane_stats())
-    L.close()
-    return out
+    return reference(case, checkpoints, wall, stats_every=stats_every)
 
 
 def gpu_channel(case, wall, precision, kernel=lbm.KERNEL_AUTO):
@@ -83,10 +61,10 @@ def test_init_matches_oracle(precision):
     ref = oracle_run(case, workload.WALL_WFB, (0,))[0]
     ch = gpu_channel(case, workload.WALL_WFB, precision)
     f = ch.populations()
-    dev_ref = ref["f"] - _W[:, None, None, None]
+    dev_ref = ref["f"] - W
     # one rounding of the deviation to the storage precision
     ulp = 2.0 ** -24 if precision == lbm.FP32 else 2.0 ** -11
-    assert np.max(np.abs((f - _W[:, None, None, None]) - dev_ref)) <= ulp * np.max(np.abs(dev_ref)) + 1e-12
+    assert np.max(np.abs((f - W) - dev_ref)) <= ulp * np.max(np.abs(dev_ref)) + 1e-12
     ch.close()
 
 
@@ -100,27 +78,14 @@ def test_parity_100_steps(wall, precision, kernel):
     case = SMALL
     checkpoints = (1, 10, 50, 100)
     ref = oracle_run(case, wall, checkpoints)
+    fl = floors(case, checkpoints, precision, wall)
     ch = gpu_channel(case, wall, precision, kernel)
     assert ch.kernel == kernel
     t = 0
-    worst = {}
     for c in checkpoints:
         ch.step(c - t)
         t = c
-        rho, u = ch.moments()
-        e_u = rel_linf(u, ref[c]["u"])
-        e_r = rel_linf(rho - 1.0, ref[c]["rho"] - 1.0)
-        worst[c] = (e_u, e_r)
-        assert e_u <= TOL[precision], (c, e_u)
-        assert e_r <= TOL_RHO[precision], (c, e_r)
-    f = ch.populations()
-    e_f = rel_linf(f - _W[:, None, None, None], ref[100]["f"] - _W[:, None, None, None])
-    assert e_f <= TOL[precision], e_f
-    if wall != workload.WALL_FREESLIP:
-        e_t = rel_linf(ch.wall_stress(), ref[100]["tw"])
-        assert e_t <= 10 * TOL[precision], e_t
-    else:
-        assert np.all(ch.wall_stress() == 0.0)
+        check_state(ch, ref[c], fl[c], precision, wall, populations=(c == 100), tag=(c, kernel))
     ch.close()
 
 
@@ -130,16 +95,13 @@ def test_parity_100_steps(wall, precision, kernel):
 def test_parity_ragged(case, wall, precision):
     checkpoints = (1, 7, 20)
     ref = oracle_run(case, wall, checkpoints)
+    fl = floors(case, checkpoints, precision, wall)
     ch = gpu_channel(case, wall, precision)
     t = 0
     for c in checkpoints:
         ch.step(c - t)
         t = c
-        rho, u = ch.moments()
-        assert rel_linf(u, ref[c]["u"]) <= TOL[precision], c
-        assert rel_linf(rho - 1.0, ref[c]["rho"] - 1.0) <= TOL_RHO[precision], c
-    if wall != workload.WALL_FREESLIP:
-        assert rel_linf(ch.wall_stress(), ref[20]["tw"]) <= 10 * TOL[precision]
+        check_state(ch, ref[c], fl[c], precision, wall, populations=(c == 20), tag=c)
     ch.close()
 
 
@@ -228,7 +190,7 @@ def test_set_populations_round_trip():
     ch = lbm.Channel.from_case(case)
     ch.set_populations(ref["f"])
     f = ch.populations()
-    dev = ref["f"] - _W[:, None, None, None]
+    dev = ref["f"] - W
     assert np.max(np.abs(f - ref["f"])) <= 2.0 ** -24 * np.max(np.abs(dev)) + 1e-15
     ch.close()
 
@@ -239,12 +201,10 @@ def test_full_size_bench_grid(precision):
     three steps compared with the oracle on every cell."""
     case = workload.CASES["c2"]
     ref = oracle_run(case, workload.WALL_WFB, (3,))[3]
+    fl = floors(case, (3,), precision, workload.WALL_WFB)[3]
     ch = gpu_channel(case, workload.WALL_WFB, precision)
     ch.step(3)
-    rho, u = ch.moments()
-    assert rel_linf(u, ref["u"]) <= TOL[precision]
-    assert rel_linf(rho - 1.0, ref["rho"] - 1.0) <= TOL_RHO[precision]
-    assert rel_linf(ch.wall_stress(), ref["tw"]) <= 10 * TOL[precision]
+    check_state(ch, ref, fl, precision, workload.WALL_WFB, populations=True)
     ch.close()
 
 

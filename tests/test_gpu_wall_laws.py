@@ -3,17 +3,15 @@ the introduction names the log law and Werner and Wengle's power law besides
 Spalding's): the CUDA path against the oracle, per wall cell over a sweep of
 R = y1 |u_t| / nu across both branches of each law, over 100 steps of a
 channel whose first layer sits in the log region, and through the batch."""
-import functools
-
 import numpy as np
 import pytest
 
 import oracle
 from paper_2009_04352_gb300 import lbm, workload
+from parity import check_state, floors, reference
 
 pytestmark = pytest.mark.gpu
 
-TOL = {lbm.FP32: 1e-5, lbm.FP16_SHIFTED: 5e-3}
 LAWS = [lbm.LAW_SPALDING, lbm.LAW_LOG, lbm.LAW_POWER]
 # first layer at y+ ~ 40, R = y+ u+ ~ 500: the log (or power) branch of every law
 CHANNEL = workload.derive_channel("wall-law channel 64x32x32", 64, 32, 32, 640.0, seed=21)
@@ -75,17 +73,6 @@ def test_wall_stress_sweep_per_cell(law, kernel):
     assert R.min() < 100 and R.max() > 1e4
 
 
-@functools.lru_cache(maxsize=None)
-def oracle_channel(case, steps):
-    L = oracle.Lattice.from_case(case)
-    L.init_channel(workload.u_mean_profile(case), workload.noise_amplitude(case), case.seed)
-    L.step(steps)
-    _, u = L.moments()
-    tw = L.wall_stress()
-    L.close()
-    return u, tw
-
-
 @pytest.mark.parametrize("kernel", [lbm.KERNEL_PAIR, lbm.KERNEL_CELL, lbm.KERNEL_QUAD, lbm.KERNEL_TMA])
 @pytest.mark.parametrize("precision", [lbm.FP32, lbm.FP16_SHIFTED])
 @pytest.mark.parametrize("law", [lbm.LAW_LOG, lbm.LAW_POWER])
@@ -93,14 +80,13 @@ def test_wall_law_parity_100_steps(law, precision, kernel):
     if kernel == lbm.KERNEL_QUAD and precision != lbm.FP16_SHIFTED:
         pytest.skip("the four-cell kernel serves FP16 storage only")
     case = CHANNEL.with_(wall_law=law)
-    u_ref, tw_ref = oracle_channel(case, 100)
+    ref = reference(case, (100,))[100]
+    fl = floors(case, (100,), precision)[100]
     ch = lbm.Channel.from_case(case, precision=precision)
     ch.set_kernel(kernel)
     ch.init_channel(workload.u_mean_profile(case), workload.noise_amplitude(case), case.seed)
     ch.step(100)
-    _, u = ch.moments()
-    assert rel(u, u_ref) <= TOL[precision]
-    assert rel(ch.wall_stress(), tw_ref) <= 10 * TOL[precision]
+    check_state(ch, ref, fl, precision, case.wall, populations=True, tag=kernel)
     ch.close()
 
 
@@ -142,8 +128,6 @@ def test_batch_members_with_mixed_laws(precision):
         assert np.array_equal(b.members[i].populations(), ch.populations()), i
         assert np.array_equal(b.members[i].wall_stress(), ch.wall_stress()), i
         ch.close()
-        u_ref, tw_ref = oracle_channel(c, 30)
-        _, u = b.members[i].moments()
-        assert rel(u, u_ref) <= TOL[precision], i
-        assert rel(b.members[i].wall_stress(), tw_ref) <= 10 * TOL[precision], i
+        check_state(b.members[i], reference(c, (30,))[30], floors(c, (30,), precision)[30], precision, c.wall,
+                    populations=True, tag=i)
     b.close()

@@ -43,12 +43,18 @@ def _profile_existing(ch):
     return st
 
 
+@pytest.mark.parametrize("start", [5, 6])
+@pytest.mark.parametrize("layout", [lbm.PULL2, lbm.AA])
 @pytest.mark.parametrize("precision", [lbm.FP32, lbm.FP16_SHIFTED])
-def test_noalloc_profile_matches_plane_stats_twice(precision):
+def test_noalloc_profile_matches_plane_stats_twice(precision, layout, start):
+    """Two calls in a row on the shared scratch. With the single-lattice AA
+    layout the state is stored under a different map after an odd and an even
+    number of steps; each comparison advances the state by one step, so either
+    start covers both maps."""
     case = workload.CASES["c1"].with_(nx=128, ny=24, nz=10)
-    ch = lbm.Channel.from_case(case, precision=precision)
+    ch = lbm.Channel.from_case(case, precision=precision, layout=layout)
     ch.init_channel(workload.u_mean_profile(case), workload.noise_amplitude(case), case.seed)
-    ch.step(5)
+    ch.step(start)
     for _ in range(2):                    # two calls in a row on the shared scratch
         got = _profile_noalloc(ch)
         ref = _profile_existing(ch)       # also advances the state by one step
