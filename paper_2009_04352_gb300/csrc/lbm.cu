@@ -216,13 +216,27 @@ cudaError_t launch_aa(lbm_handle *h, cudaStream_t s, bool stats)
 {
     const dim3 grid = step_grid(h), block(h->bx);
     void *f = h->f[0];
+#ifndef LBM_QUAD_AA_SPLIT
+#define LBM_QUAD_AA_SPLIT 0   // 1: interior and wall-row launches (measured slower in place)
+#endif
     if (h->kernel == LBM_KERNEL_QUAD) {
-        // one launch over every row (an interior / wall-row split, as in the
-        // two-lattice step, measured slower for the in-place steps)
         __half *fh = (__half *)f;
-        return stats ? launch_pdl(lbm::k_step_quad_aa<true, COLL, LAY>, grid, block, 0, s, fh, h->g, h->p, h->tw, h->part)
-                     : launch_pdl(lbm::k_step_quad_aa<false, COLL, LAY>, grid, block, 0, s, fh, h->g, h->p, h->tw,
-                                  h->part);
+        if (!LBM_QUAD_AA_SPLIT || h->g.ny <= 2)
+            return stats ? launch_pdl(lbm::k_step_quad_aa<true, COLL, LAY>, grid, block, 0, s, fh, h->g, h->p, h->tw,
+                                      h->part)
+                         : launch_pdl(lbm::k_step_quad_aa<false, COLL, LAY>, grid, block, 0, s, fh, h->g, h->p, h->tw,
+                                      h->part);
+        // interior rows, then the two wall rows with the two-cell tile
+        const dim3 gi(grid.x, h->g.ny - 2, grid.z), gw(grid.x, 2, grid.z), bw(2 * h->bx);
+        cudaError_t e = stats ? launch_pdl(lbm::k_step_quad_aa<true, COLL, LAY, lbm::ROWS_INTERIOR>, gi, block, 0, s,
+                                           fh, h->g, h->p, h->tw, h->part)
+                              : launch_pdl(lbm::k_step_quad_aa<false, COLL, LAY, lbm::ROWS_INTERIOR>, gi, block, 0, s,
+                                           fh, h->g, h->p, h->tw, h->part);
+        if (e != cudaSuccess) return e;
+        return stats ? launch_pdl(lbm::k_step_pair_wall<__half, true, COLL, LAY>, gw, bw, 0, s, fh, fh, h->g, h->p,
+                                  h->tw, h->part)
+                     : launch_pdl(lbm::k_step_pair_wall<__half, false, COLL, LAY>, gw, bw, 0, s, fh, fh, h->g, h->p,
+                                  h->tw, h->part);
     }
     if (h->kernel == LBM_KERNEL_PAIR) {
         if (h->precision == LBM_FP16_SHIFTED) {
@@ -281,7 +295,10 @@ int launch_step_c(lbm_handle *h, cudaStream_t s, int src, bool stats)
         // interior-only instantiation spills more than the combined one)
         const __half *ah = (const __half *)a;
         __half *bh = (__half *)b;
-        if (COLL != lbm::COLL_BGK) {
+#ifndef LBM_QUAD_MRT_SPLIT
+#define LBM_QUAD_MRT_SPLIT 1
+#endif
+        if (COLL != lbm::COLL_BGK && !LBM_QUAD_MRT_SPLIT) {
             e = stats ? launch_pdl(lbm::k_step_quad<true, COLL, lbm::ROWS_ALL>, grid, block, 0, s, ah, bh, h->g,
                                    h->p, h->tw, h->part)
                       : launch_pdl(lbm::k_step_quad<false, COLL, lbm::ROWS_ALL>, grid, block, 0, s, ah, bh, h->g,
@@ -295,7 +312,7 @@ int launch_step_c(lbm_handle *h, cudaStream_t s, int src, bool stats)
         }
         // the wall rows with the two-cell tile in CTAs of twice the threads
         const dim3 gw(grid.x, 2, grid.z), bw(2 * h->bx);
-        if (COLL == lbm::COLL_BGK && e == cudaSuccess)
+        if ((COLL == lbm::COLL_BGK || LBM_QUAD_MRT_SPLIT) && e == cudaSuccess)
             e = stats ? launch_pdl(lbm::k_step_pair_wall<__half, true, COLL>, gw, bw, 0, s, ah, bh, h->g, h->p, h->tw,
                                    h->part)
                       : launch_pdl(lbm::k_step_pair_wall<__half, false, COLL>, gw, bw, 0, s, ah, bh, h->g, h->p, h->tw,
@@ -502,28 +519,22 @@ int lbm_create_handle(lbm_grid g, double tau, double C_s, const double force[3],
     }
     h->p.t02 = (float)((double)h->p.tau0 * (double)h->p.tau0);
     h->nu_wall = nu;
-    // MRT constants: ghost rates after d'Humieres et al. (2002) and the Guo
-    // forcing in moment space, M G = gc + gu . u with
-    // G_a = w_a [3 e_a.F + (9 (e_a.u)(e_a.F) - 3 u.F)]
+    // MRT constants: rates of the ghost groups after d'Humieres et al. (2002),
+    // s_e 1.19, s_eps 1.4, s_m 1.98, with s_q 1.99 (linear stability near
+    // tau0 = 1/2); the stress and pi moments relax with 1/tau_eff. The device
+    // correction of group g is (omega - s_g) c_g times a bracket of pair sums
+    // (mrt_ghost_pair), c_g = 19 / |row 1|^2, 1 / |row 2|^2, (10/3) / |row 4|^2,
+    // 2 / |row 16|^2 from the basis norms.
     h->p.collision = lbm::COLL_BGK;
     h->p.vd_scale = 0.f;
-    for (int i = 0; i < lbm::Q; ++i) {
-        double r = 1.0;
-        if (i == 1) r = 1.19;
-        if (i == 2) r = 1.4;   // rows 10 and 12 relax with 1/tau_eff (mrt_stress)
-        if (i == 4 || i == 6 || i == 8) r = 1.99;   // q: linear stability near tau0 = 1/2
-        if (i >= 16) r = 1.98;
-        h->p.mrt_s[i] = (float)r;
-        double gc = 0.0, gu[3] = {0.0, 0.0, 0.0};
-        for (int a = 0; a < lbm::Q; ++a) {
-            const int e[3] = {lbm::ex_of(a), lbm::ey_of(a), lbm::ez_of(a)};
-            const double eF = e[0] * force[0] + e[1] * force[1] + e[2] * force[2];
-            const double w = lbm::w_of(a), c = lbm::mrt_coef(i, a);
-            gc += c * 3.0 * w * eF;
-            for (int al = 0; al < 3; ++al) gu[al] += c * w * (9.0 * e[al] * eF - 3.0 * force[al]);
+    {
+        const double rate[4] = {1.19, 1.4, 1.99, 1.98};
+        const double cg[4] = {19.0 / lbm::mrt_norm(1), 1.0 / lbm::mrt_norm(2), (10.0 / 3.0) / lbm::mrt_norm(4),
+                              2.0 / lbm::mrt_norm(16)};
+        for (int k = 0; k < 4; ++k) {
+            h->p.mrt_a[k] = (float)cg[k];
+            h->p.mrt_b[k] = (float)(-rate[k] * cg[k]);
         }
-        h->p.mrt_gc[i] = (float)gc;
-        for (int al = 0; al < 3; ++al) h->p.mrt_gu[i][al] = (float)gu[al];
     }
     h->precision = precision;
     h->layout = layout;

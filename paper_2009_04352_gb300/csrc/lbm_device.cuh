@@ -102,9 +102,11 @@ struct Phys {
     // LES model
     int collision;       // COLL_BGK or COLL_MRT
     float vd_scale;      // van Driest: u_tau / (nu A+); 0 = no damping
-    float mrt_s[19];     // MRT rates of the ghost moments (stress moments relax with 1/tau_eff)
-    float mrt_gc[19];    // Guo forcing in moment space, M G = gc + gu . u
-    float mrt_gu[19][3];
+    // MRT: ghost groups e, eps, q, m (rates s_g different from 1/tau_eff);
+    // the correction factor of group g is omega a_g + b_g = (omega - s_g) c_g
+    // (c_g from the basis norms, mrt_ghost_pair in lbm_pair.cuh)
+    float mrt_a[4];
+    float mrt_b[4];
 };
 
 enum { COLL_BGK = 0, COLL_MRT = 1 };
@@ -148,18 +150,14 @@ __host__ __device__ constexpr int mrt_norm(int i)
     return n;
 }
 
-// Moments relaxed with 1/tau_eff (the viscous stress: 3p_xx, p_ww, p_xy, p_yz, p_xz).
-// Rows relaxing with 1/tau_eff: the five stress moments and the two
-// fourth-order pi moments (10, 12). With the published pi rate of 1.4 the
-// scheme is linearly unstable for tau0 below about 0.502, where the channel
-// runs operate (the host also sets the q rates to 1.99 for the same reason).
-__host__ __device__ constexpr bool mrt_stress(int i)
-{
-    return i == 9 || i == 10 || i == 11 || i == 12 || i == 13 || i == 14 || i == 15;
-}
-// Non-conserved moments even (odd) under e -> -e.
-__host__ __device__ constexpr bool mrt_even_ghost(int i) { return i == 1 || i == 2 || (i >= 9 && i <= 15); }
-__host__ __device__ constexpr bool mrt_odd_ghost(int i) { return i == 4 || i == 6 || i == 8 || i >= 16; }
+// Ghost groups of the basis whose rates differ from 1/tau_eff: the energy e
+// (row 1), its square eps (row 2), the energy fluxes q (rows 4, 6, 8) and the
+// third-order m (rows 16-18). The five stress moments (rows 9, 11, 13-15) and
+// the two fourth-order pi moments (rows 10, 12) relax with 1/tau_eff, as in
+// BGK: with the published pi rate of 1.4 the scheme is linearly unstable for
+// tau0 below about 0.502, where the channel runs operate (the q rates are
+// raised to 1.99 for the same reason).
+enum { MRT_E = 0, MRT_EPS = 1, MRT_Q = 2, MRT_M = 3 };
 
 // Smagorinsky coefficient of layer y with the van Driest factor
 // D = 1 - exp(-y+/A+) of the layer centre (j + 1/2 from the nearer wall).

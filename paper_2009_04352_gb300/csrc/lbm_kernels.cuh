@@ -81,60 +81,55 @@ __device__ __forceinline__ CellState collide(const float (&f)[Q], float (&fs)[Q]
     const float gk = 1.f - 0.5f * omega;
 
     const float usq = ux * ux + uy * uy + uz * uz;
+    const float uF = fmaf(ux, p.Fx, fmaf(uy, p.Fy, uz * p.Fz));
+    // MRT (d'Humieres et al. 2002): BGK plus the corrections of the ghost
+    // groups e, eps, q, m whose rates differ from omega (mrt_ghost_pair in
+    // lbm_pair.cuh states the brackets); the pair k of the loop below then
+    // changes by ge[k] in its half sum and go[k] in its half difference
+    float ge_ax = 0.f, ge_dg = 0.f, ge_rest = 0.f, go[9];
     if constexpr (COLL == COLL_MRT) {
-        // MRT (d'Humieres et al. 2002): ghost and stress moments of f - f^eq
-        // relax with their rates; Guo forcing in moment space (gc + gu . u)
-        float n[Q];
+        float hs[9], hd[9];
 #pragma unroll
-        for (int a = 0; a < Q; ++a) {
-            const float eu = ex_of(a) * ux + ey_of(a) * uy + ez_of(a) * uz;
-            n[a] = f[a] - (float)w_of(a) * (m.drho + rho * (3.f * eu + 4.5f * eu * eu - 1.5f * usq));
+        for (int k = 0; k < 9; ++k) {
+            hs[k] = 0.5f * (f[2 * k + 1] + f[2 * k + 2]);
+            hd[k] = 0.5f * (f[2 * k + 1] - f[2 * k + 2]);
         }
-        float dm[Q];
-#pragma unroll
-        for (int i = 1; i < Q; ++i) {
-            dm[i] = 0.f;
-            if (!mrt_even_ghost(i) && !mrt_odd_ghost(i)) continue;
-            float mi = 0.f;
-#pragma unroll
-            for (int a = 0; a < Q; ++a)
-                if (mrt_coef(i, a) != 0) mi += (float)mrt_coef(i, a) * n[a];
-            const float g = p.mrt_gc[i] + p.mrt_gu[i][0] * ux + p.mrt_gu[i][1] * uy + p.mrt_gu[i][2] * uz;
-            const float sr = mrt_stress(i) ? omega : p.mrt_s[i];
-            dm[i] = (-sr * mi + (1.f - 0.5f * sr) * g) / (float)mrt_norm(i);
-        }
-        float mass = 0.f, mx = 0.f, my = 0.f, mz = 0.f;
-#pragma unroll
-        for (int a = 1; a < Q; ++a) {
-            float d = 0.f;
-#pragma unroll
-            for (int i = 1; i < Q; ++i)
-                if ((mrt_even_ghost(i) || mrt_odd_ghost(i)) && mrt_coef(i, a) != 0) d += (float)mrt_coef(i, a) * dm[i];
-            fs[a] = f[a] + d;
-            mass += d;
-            mx += ex_of(a) * d;
-            my += ey_of(a) * d;
-            mz += ez_of(a) * d;
-        }
-        // exact momentum F and mass 0 of the update
-        const float cx = 0.5f * (p.Fx - mx), cy = 0.5f * (p.Fy - my), cz = 0.5f * (p.Fz - mz);
-        fs[1] += cx;
-        fs[2] -= cx;
-        fs[3] += cy;
-        fs[4] -= cy;
-        fs[5] += cz;
-        fs[6] -= cz;
-        fs[0] = f[0] - mass;
-        return c;
+        const float A = hs[0] + hs[1] + hs[2];
+        const float D = ((hs[3] + hs[4]) + (hs[5] + hs[6])) + (hs[7] + hs[8]);
+        const float du = rho * usq - uF;
+        const float ce = fmaf(omega, p.mrt_a[MRT_E], p.mrt_b[MRT_E]) * ((2.f * D - f[0]) - du);
+        const float cp = fmaf(omega, p.mrt_a[MRT_EPS], p.mrt_b[MRT_EPS]) *
+                         fmaf(9.f, f[0], fmaf(-14.f, A, fmaf(-4.f, D, 5.5f * du)));
+        ge_ax = fmaf(-11.f, ce, -4.f * cp);
+        ge_dg = fmaf(8.f, ce, cp);
+        ge_rest = fmaf(-30.f, ce, 12.f * cp);
+        const float kq = fmaf(omega, p.mrt_a[MRT_Q], p.mrt_b[MRT_Q]);
+        const float km = fmaf(omega, p.mrt_a[MRT_M], p.mrt_b[MRT_M]);
+        const float qx = kq * (((hd[3] + hd[4]) + (hd[6] + hd[7])) - 2.f * hd[0]);
+        const float qy = kq * (((hd[3] + hd[5]) + (hd[8] - hd[6])) - 2.f * hd[1]);
+        const float qz = kq * (((hd[4] + hd[5]) - (hd[7] + hd[8])) - 2.f * hd[2]);
+        const float mx = km * ((hd[3] + hd[6]) - (hd[4] + hd[7]));
+        const float my = km * (((hd[5] + hd[6]) + hd[8]) - hd[3]);
+        const float mz = km * ((hd[4] + hd[8]) - (hd[5] + hd[7]));
+        go[0] = -4.f * qx;
+        go[1] = -4.f * qy;
+        go[2] = -4.f * qz;
+        go[3] = (qx + qy) + (mx - my);
+        go[4] = (qx + qz) + (mz - mx);
+        go[5] = (qy + qz) + (my - mz);
+        go[6] = (qx - qy) + (mx + my);
+        go[7] = (qx - qz) - (mx + mz);
+        go[8] = (qy - qz) + (my + mz);
     }
     // BGK (see the comment above the struct): weights scaled by 36, o36 = omega / 36
-    const float uF = fmaf(ux, p.Fx, fmaf(uy, p.Fy, uz * p.Fz));
     const float S0 = fmaf(-1.5f, rho * usq, m.drho);   // isotropic part of (f^eq - w) / w
     const float o36 = omega * (1.f / 36.f);
     const float r45 = 4.5f * rho;
     const float g9 = 0.25f * gk, g3 = (1.f / 12.f) * gk;   // 9 gk / 36, 3 gk / 36
     const float mgu = (-1.f / 12.f) * gk * uF;              // -3 gk u.F / 36
-    fs[0] = f[0] + fmaf(o36, fmaf(-36.f, f[0], 12.f * S0), 12.f * mgu);
+    float d0 = fmaf(o36, fmaf(-36.f, f[0], 12.f * S0), 12.f * mgu);
+    if constexpr (COLL == COLL_MRT) d0 += ge_rest;
+    fs[0] = f[0] + d0;
     float de[9], dd[9];
     float mx = 0.f, my = 0.f, mz = 0.f;
 #pragma unroll
@@ -151,6 +146,10 @@ __device__ __forceinline__ CellState collide(const float (&f)[Q], float (&fs)[Q]
         const float nd = fmaf(3.f * W, ej, fmaf(-36.f, fo, 1.5f * WeF));
         de[k] = fmaf(o36, ne, fmaf(g9 * WeF, eu, W * mgu));
         dd[k] = fmaf(o36, nd, g3 * WeF);
+        if constexpr (COLL == COLL_MRT) {
+            de[k] += k < 3 ? ge_ax : ge_dg;
+            dd[k] += go[k];
+        }
         if (ex_of(a)) mx += ex_of(a) * dd[k];
         if (ey_of(a)) my += ey_of(a) * dd[k];
         if (ez_of(a)) mz += ez_of(a) * dd[k];

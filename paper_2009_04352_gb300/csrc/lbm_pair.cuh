@@ -215,6 +215,73 @@ __device__ __forceinline__ void wall_layer_pair(float2 (&f)[Q], const PairState 
     }
 }
 
+// MRT of d'Humieres et al. (2002), written as the BGK update plus the
+// corrections of the ghost moments whose rates differ from omega = 1/tau_eff:
+// the energy e (s_e), its square eps (s_eps), the energy fluxes q (s_q) and
+// the third-order moments m (s_m); the stress and fourth-order pi moments
+// relax with omega as in BGK. With the orthogonal basis rows phi_i, moving
+// moment i from the BGK change -omega m_i^neq + (1 - omega/2) g_i to the MRT
+// change -s_i m_i^neq + (1 - s_i/2) g_i (g_i the moment of the Guo force term)
+// adds C_i phi_i to the populations, C_i = (omega - s_i)(m_i^neq + g_i/2)/|phi_i|^2.
+// On the pair half sums hs_k and half differences hd_k of the deviations,
+// with A and D the sums of hs over the axis and the diagonal pairs and Guo's
+// rho u = j + F/2, the brackets m_i^neq + g_i/2 are
+//   e:    19 (2 D - f_0 - rho u.u + u.F)
+//   eps:  9 f_0 - 14 A - 4 D + 11/2 (rho u.u - u.F)
+//   q_x:  10/3 (sum of hd over the four diagonal pairs with e_x != 0, signed
+//         by e_x of the pair's first member, - 2 hd_x)  (the equilibrium and
+//         force parts cancel; q_y, q_z alike)
+//   m_x:  2 (hd_(1,1,0) - hd_(1,0,1) + hd_(1,-1,0) - hd_(1,0,-1))  (m_y, m_z alike)
+// and the change of a pair's half sum is phi_e C_e + phi_eps C_eps of its
+// class (axis -11, -4; diagonal 8, 1; rest -30, 12), of its half difference
+// the sum of phi_i C_i over q and m for its first member.
+struct MrtPair {
+    float2 ea, ed, er;     // half-sum change of an axis / diagonal pair, change of the rest population
+    float2 cq[3], cm[3];   // C of q_x, q_y, q_z and m_x, m_y, m_z
+};
+
+__device__ __forceinline__ MrtPair mrt_ghost_pair(const float2 (&hs)[9], const float2 (&hd)[9], float2 f0,
+                                                  float2 rusq, float2 uF, float2 omega, const Phys &p)
+{
+    MrtPair m;
+    const float2 A = add2(add2(hs[0], hs[1]), hs[2]);
+    const float2 D = add2(add2(add2(hs[3], hs[4]), add2(hs[5], hs[6])), add2(hs[7], hs[8]));
+    const float2 ke = fma2(omega, bc(p.mrt_a[MRT_E]), bc(p.mrt_b[MRT_E]));
+    const float2 kp = fma2(omega, bc(p.mrt_a[MRT_EPS]), bc(p.mrt_b[MRT_EPS]));
+    const float2 kq = fma2(omega, bc(p.mrt_a[MRT_Q]), bc(p.mrt_b[MRT_Q]));
+    const float2 km = fma2(omega, bc(p.mrt_a[MRT_M]), bc(p.mrt_b[MRT_M]));
+    const float2 du = sub2(rusq, uF);
+    const float2 ce = mul2(ke, sub2(sub2(add2(D, D), f0), du));
+    const float2 cp = mul2(kp, fma2(bc(9.f), f0, fma2(bc(-14.f), A, fma2(bc(-4.f), D, mul2(bc(5.5f), du)))));
+    m.ea = fma2(bc(-11.f), ce, mul2(bc(-4.f), cp));
+    m.ed = fma2(bc(8.f), ce, cp);
+    m.er = fma2(bc(-30.f), ce, mul2(bc(12.f), cp));
+    // pairs 3..8: first members (1,1,0), (1,0,1), (0,1,1), (1,-1,0), (1,0,-1), (0,1,-1)
+    m.cq[0] = mul2(kq, sub2(add2(add2(hd[3], hd[4]), add2(hd[6], hd[7])), add2(hd[0], hd[0])));
+    m.cq[1] = mul2(kq, sub2(add2(add2(hd[3], hd[5]), sub2(hd[8], hd[6])), add2(hd[1], hd[1])));
+    m.cq[2] = mul2(kq, sub2(sub2(add2(hd[4], hd[5]), add2(hd[7], hd[8])), add2(hd[2], hd[2])));
+    m.cm[0] = mul2(km, sub2(add2(hd[3], hd[6]), add2(hd[4], hd[7])));
+    m.cm[1] = mul2(km, sub2(add2(add2(hd[5], hd[6]), hd[8]), hd[3]));
+    m.cm[2] = mul2(km, sub2(add2(hd[4], hd[8]), add2(hd[5], hd[7])));
+    return m;
+}
+
+// dd + the half-difference change of pair k from the q and m corrections.
+__device__ __forceinline__ float2 mrt_odd_add(const MrtPair &m, int k, float2 dd)
+{
+    switch (k) {
+    case 0: return fma2(bc(-4.f), m.cq[0], dd);
+    case 1: return fma2(bc(-4.f), m.cq[1], dd);
+    case 2: return fma2(bc(-4.f), m.cq[2], dd);
+    case 3: return add2(dd, add2(add2(m.cq[0], m.cq[1]), sub2(m.cm[0], m.cm[1])));
+    case 4: return add2(dd, add2(add2(m.cq[0], m.cq[2]), sub2(m.cm[2], m.cm[0])));
+    case 5: return add2(dd, add2(add2(m.cq[1], m.cq[2]), sub2(m.cm[1], m.cm[2])));
+    case 6: return add2(dd, add2(sub2(m.cq[0], m.cq[1]), add2(m.cm[0], m.cm[1])));
+    case 7: return add2(dd, sub2(sub2(m.cq[0], m.cq[2]), add2(m.cm[0], m.cm[2])));
+    default: return add2(dd, add2(sub2(m.cq[1], m.cq[2]), add2(m.cm[1], m.cm[2])));
+    }
+}
+
 // collide() of lbm_kernels.cuh for two cells (in place: f becomes f*),
 // organised around the opposite pairs k = 0..8 (directions 2k+1, 2k+2):
 // s_k = f_a + f_b and d_k = f_a - f_b carry all moments the update needs,
@@ -298,101 +365,12 @@ __device__ __forceinline__ PairState collide_pair(float2 (&f)[Q], const Phys &p,
         omega = make_float2(2.f / __fadd_rn(p.tau0, sqrtf(__fadd_rn(t02, cqx))),
                             2.f / __fadd_rn(p.tau0, sqrtf(__fadd_rn(t02, cqy))));
     }
-    if constexpr (COLL == COLL_MRT) {
-        // MRT (d'Humieres et al. 2002) on the pair sums s = 2 hs and differences
-        // d = 2 hd: non-equilibrium n = s - s^eq, d - d^eq, f0 - f0^eq with
-        //   s^eq = 2 w (S0 + 9/2 rho (e.u)^2), d^eq = 6 w rho (e.u), f0^eq = S0 / 3,
-        // ghost/stress moments m_i = sum coef(i, a) n_a, then
-        //   dm_i = [-s_i m_i + (1 - s_i/2)(gc_i + gu_i . u)] / |row i|^2
-        // and back to the pairs with the same coefficients (orthogonal basis).
-        const float2 usq = fma2(ux, ux, fma2(uy, uy, mul2(uz, uz)));
-        const float2 S0 = fma2(bc(-1.5f), mul2(rho, usq), drho);
-        const float2 r45 = mul2(bc(4.5f), rho), r6 = mul2(bc(6.f), rho);
-        const float2 eus[9] = {ux, uy, uz, add2(ux, uy), add2(ux, uz), add2(uy, uz),
-                               sub2(ux, uy), sub2(ux, uz), sub2(uy, uz)};
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            const float w2 = k < 3 ? 2.f / 18.f : 2.f / 36.f;   // 2 w
-            const float2 seq = mul2(bc(w2), fma2(mul2(r45, eus[k]), eus[k], S0));
-            const float2 deq = mul2(bc(0.5f * w2), mul2(r6, eus[k]));
-            hs[k] = sub2(add2(hs[k], hs[k]), seq);   // now the non-equilibrium pair sum
-            hd[k] = sub2(add2(hd[k], hd[k]), deq);   // and difference
-        }
-        const float2 n0 = fma2(bc(-1.f / 3.f), S0, f[0]);
-        float2 dm[Q];
-#pragma unroll
-        for (int i = 1; i < Q; ++i) {
-            if (!mrt_even_ghost(i) && !mrt_odd_ghost(i)) continue;
-            float2 m = bc(0.f);
-            bool first = true;
-            if (mrt_even_ghost(i) && mrt_coef(i, 0) != 0) {
-                m = mul2(bc((float)mrt_coef(i, 0)), n0);
-                first = false;
-            }
-#pragma unroll
-            for (int k = 0; k < 9; ++k) {
-                const int c = mrt_coef(i, 2 * k + 1);
-                if (c == 0) continue;
-                const float2 x = mrt_even_ghost(i) ? hs[k] : hd[k];
-                if (first) {
-                    m = c == 1 ? x : (c == -1 ? mul2(bc(-1.f), x) : mul2(bc((float)c), x));
-                    first = false;
-                } else {
-                    m = c == 1 ? add2(m, x) : (c == -1 ? sub2(m, x) : fma2(bc((float)c), x, m));
-                }
-            }
-            float2 g = bc(p.mrt_gc[i]);
-            if (mrt_even_ghost(i))
-                g = fma2(bc(p.mrt_gu[i][0]), ux, fma2(bc(p.mrt_gu[i][1]), uy, fma2(bc(p.mrt_gu[i][2]), uz, g)));
-            const float inv = 1.f / (float)mrt_norm(i);
-            if (mrt_stress(i)) {
-                const float2 gs = fma2(bc(-0.5f), omega, bc(1.f));   // 1 - s/2
-                dm[i] = mul2(bc(inv), fma2(gs, g, mul2(mul2(bc(-1.f), omega), m)));
-            } else {
-                const float sr = p.mrt_s[i];
-                dm[i] = mul2(bc(inv), fma2(bc(1.f - 0.5f * sr), g, mul2(bc(-sr), m)));
-            }
-        }
-        // back to the pairs: s' = n_s + s^eq + ds, d' = n_d + d^eq + dd
-        float2 mass, mx, my, mz;
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            const int a = 2 * k + 1;
-            float2 ds = bc(0.f), dd = bc(0.f);
-#pragma unroll
-            for (int i = 1; i < Q; ++i) {
-                const int c = mrt_coef(i, a);
-                if (c == 0) continue;
-                if (mrt_even_ghost(i)) ds = fma2(bc(2.f * c), dm[i], ds);
-                if (mrt_odd_ghost(i)) dd = fma2(bc(2.f * c), dm[i], dd);
-            }
-            const float w2 = k < 3 ? 2.f / 18.f : 2.f / 36.f;
-            const float2 seq = mul2(bc(w2), fma2(mul2(r45, eus[k]), eus[k], S0));
-            const float2 deq = mul2(bc(0.5f * w2), mul2(r6, eus[k]));
-            // ds, dd are the changes of the pair sum and difference
-            mass = k == 0 ? ds : add2(mass, ds);
-            const float2 hdd = mul2(bc(0.5f), dd);
-            if (k == 0) mx = hdd;
-            else if (ex_of(a)) mx = ex_of(a) > 0 ? add2(mx, hdd) : sub2(mx, hdd);
-            if (k == 1) my = hdd;
-            else if (k > 1 && ey_of(a)) my = ey_of(a) > 0 ? add2(my, hdd) : sub2(my, hdd);
-            if (k == 2) mz = hdd;
-            else if (k > 2 && ez_of(a)) mz = ez_of(a) > 0 ? add2(mz, hdd) : sub2(mz, hdd);
-            hs[k] = mul2(bc(0.5f), add2(add2(hs[k], seq), ds));
-            hd[k] = mul2(bc(0.5f), add2(add2(hd[k], deq), dd));
-        }
-        // exact momentum F (the j rows) and mass (rest population) of the update
-        hd[0] = add2(hd[0], sub2(bc(p.hF[0]), mx));
-        hd[1] = add2(hd[1], sub2(bc(p.hF[1]), my));
-        hd[2] = add2(hd[2], sub2(bc(p.hF[2]), mz));
-        f[0] = sub2(f[0], mass);
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            f[2 * k + 1] = add2(hs[k], hd[k]);
-            f[2 * k + 2] = sub2(hs[k], hd[k]);
-        }
-        return c;
-    } else if constexpr (EXACT_W) {
+    const float2 usq = fma2(ux, ux, fma2(uy, uy, mul2(uz, uz)));
+    const float2 uF = fma2(ux, bc(p.Fx), fma2(uy, bc(p.Fy), mul2(uz, bc(p.Fz))));
+    // MRT: corrections of the ghost groups (zero cost for BGK)
+    MrtPair mg;
+    if constexpr (COLL == COLL_MRT) mg = mrt_ghost_pair(hs, hd, f[0], mul2(rho, usq), uF, omega, p);
+    if constexpr (EXACT_W) {
     // BGK with the weights scaled by 36 (36 w = 12 rest, 2 axis, 1 diagonal:
     // exact) and 1/36 folded into the rate, o36 = omega / 36. Per pair, with
     // W = 36 w, the non-equilibrium difference is formed before the rate
@@ -409,8 +387,6 @@ __device__ __forceinline__ PairState collide_pair(float2 (&f)[Q], const Phys &p,
     // change is zero up to unbiased roundings.
     const float2 gk = fma2(bc(-0.5f), omega, bc(1.f));
     const float2 o36 = mul2(omega, bc(1.f / 36.f));
-    const float2 usq = fma2(ux, ux, fma2(uy, uy, mul2(uz, uz)));
-    const float2 uF = fma2(ux, bc(p.Fx), fma2(uy, bc(p.Fy), mul2(uz, bc(p.Fz))));
     const float2 S0 = fma2(bc(-1.5f), mul2(rho, usq), drho);
     const float2 r45 = mul2(bc(4.5f), rho);
     const float2 r45a = add2(r45, r45), S0a = add2(S0, S0);               // W = 2 (exact doublings)
@@ -424,7 +400,9 @@ __device__ __forceinline__ PairState collide_pair(float2 (&f)[Q], const Phys &p,
                            sub2(ux, uy), sub2(ux, uz), sub2(uy, uz)};
     const float2 ejs[9] = {jx, jy, jz, add2(jx, jy), add2(jx, jz), add2(jy, jz),
                            sub2(jx, jy), sub2(jx, jz), sub2(jy, jz)};
-    f[0] = add2(f[0], fma2(o36, fma2(bc(-36.f), f[0], mul2(bc(12.f), S0)), mul2(bc(12.f), mgu)));
+    float2 d0 = fma2(o36, fma2(bc(-36.f), f[0], mul2(bc(12.f), S0)), mul2(bc(12.f), mgu));
+    if constexpr (COLL == COLL_MRT) d0 = add2(d0, mg.er);
+    f[0] = add2(f[0], d0);
     float2 mx, my, mz;
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
@@ -435,8 +413,12 @@ __device__ __forceinline__ PairState collide_pair(float2 (&f)[Q], const Phys &p,
         const float2 WeF = bc(p.WeF[k]);      // 36 w (e.F)
         const float2 ne = fma2(mul2(axis ? r45a : r45, eu), eu, fma2(bc(-36.f), hs[k], axis ? S0a : S0));
         const float2 nd = fma2(bc(W3), ejs[k], fma2(bc(-36.f), hd[k], mul2(bc(1.5f), WeF)));
-        const float2 de = fma2(o36, ne, fma2(mul2(g9, WeF), eu, axis ? mgua : mgu));
-        const float2 dd = fma2(o36, nd, mul2(g3, WeF));
+        float2 de = fma2(o36, ne, fma2(mul2(g9, WeF), eu, axis ? mgua : mgu));
+        float2 dd = fma2(o36, nd, mul2(g3, WeF));
+        if constexpr (COLL == COLL_MRT) {
+            de = add2(de, axis ? mg.ea : mg.ed);
+            dd = mrt_odd_add(mg, k, dd);
+        }
         if (k == 0) mx = dd;
         else if (ex_of(a)) mx = ex_of(a) > 0 ? add2(mx, dd) : sub2(mx, dd);
         if (k == 1) my = dd;
@@ -461,8 +443,6 @@ __device__ __forceinline__ PairState collide_pair(float2 (&f)[Q], const Phys &p,
     // population (the storage form of FP16, whose rounding dominates)
     const float2 gk = fma2(bc(-0.5f), omega, bc(1.f));
     const float2 nw = mul2(bc(-1.f), omega);                               // -omega
-    const float2 usq = fma2(ux, ux, fma2(uy, uy, mul2(uz, uz)));
-    const float2 uF = fma2(ux, bc(p.Fx), fma2(uy, bc(p.Fy), mul2(uz, bc(p.Fz))));
     const float2 S0 = fma2(bc(-1.5f), mul2(rho, usq), drho);
     const float2 oS = sub2(mul2(omega, S0), mul2(mul2(bc(3.f), gk), uF));  // omega S0 - 3 gk u.F
     const float2 oR45 = mul2(omega, mul2(bc(4.5f), rho));                // 4.5 omega rho
@@ -485,8 +465,12 @@ __device__ __forceinline__ PairState collide_pair(float2 (&f)[Q], const Phys &p,
         const float2 eF = bc(p.weF[k]);   // w e.F
         const float2 Gk = mul2(g9, eF), Hk = mul2(g3, eF);
         // with s = 2 hs and d = 2 hd: -omega s / 2 = -omega hs
-        const float2 de = fma2(nw, hs[k], fma2(fma2(axis ? Aa : Ad, eu, Gk), eu, axis ? Ca : Cd));
-        const float2 dd = fma2(nw, hd[k], fma2(axis ? Da : Dd, eu, Hk));
+        float2 de = fma2(nw, hs[k], fma2(fma2(axis ? Aa : Ad, eu, Gk), eu, axis ? Ca : Cd));
+        float2 dd = fma2(nw, hd[k], fma2(axis ? Da : Dd, eu, Hk));
+        if constexpr (COLL == COLL_MRT) {
+            de = add2(de, axis ? mg.ea : mg.ed);
+            dd = mrt_odd_add(mg, k, dd);
+        }
         // accumulate sum de and sum e dd (first terms: pairs 0, 1, 2 are the axes)
         mass = k == 0 ? de : add2(mass, de);
         if (k == 0) mx = dd;
@@ -648,9 +632,12 @@ __device__ __forceinline__ void pdl_begin()
 #ifndef LBM_PAIR_MIN_BLOCKS
 #define LBM_PAIR_MIN_BLOCKS 6   // resident CTAs per SM the register budget must allow (80 registers)
 #endif
+#ifndef LBM_PAIR_MRT_MIN_BLOCKS
+#define LBM_PAIR_MRT_MIN_BLOCKS 5   // the same for the MRT instantiations (96 registers)
+#endif
 
 template <typename T, bool STATS, int COLL = COLL_BGK>
-__global__ void __launch_bounds__(128, LBM_PAIR_MIN_BLOCKS) k_step_pair(const T *__restrict__ src, T *__restrict__ dst, Geom g, Phys p,
+__global__ void __launch_bounds__(128, COLL == COLL_MRT ? LBM_PAIR_MRT_MIN_BLOCKS : LBM_PAIR_MIN_BLOCKS) k_step_pair(const T *__restrict__ src, T *__restrict__ dst, Geom g, Phys p,
                                                    float *__restrict__ tw_out, double *__restrict__ part)
 {
     pdl_begin();
@@ -679,7 +666,7 @@ __global__ void __launch_bounds__(256) k_step_pair_wall(const T *src, T *dst, Ge
 
 // The two-cell step on the single AA array (LAY_AA_EVEN or LAY_AA_ODD).
 template <typename T, bool STATS, int COLL, int LAY>
-__global__ void __launch_bounds__(128, LBM_PAIR_MIN_BLOCKS) k_step_pair_aa(T *f, Geom g, Phys p,
+__global__ void __launch_bounds__(128, COLL == COLL_MRT ? LBM_PAIR_MRT_MIN_BLOCKS : LBM_PAIR_MIN_BLOCKS) k_step_pair_aa(T *f, Geom g, Phys p,
                                                                             float *__restrict__ tw_out,
                                                                             double *__restrict__ part)
 {

@@ -214,6 +214,12 @@ __device__ __forceinline__ void quad_half(uint2 (&r)[Q], const Phys &p, float sm
 #ifndef LBM_QUAD_MIN_BLOCKS
 #define LBM_QUAD_MIN_BLOCKS 5   // resident CTAs per SM the register budget must allow
 #endif
+#ifndef LBM_QUAD_MRT_MIN_BLOCKS
+#define LBM_QUAD_MRT_MIN_BLOCKS 4   // the same for the MRT instantiations (128 registers)
+#endif
+#ifndef LBM_QUAD_AA_MIN_BLOCKS
+#define LBM_QUAD_AA_MIN_BLOCKS 4    // the same for the in-place AA steps with BGK (128 registers)
+#endif
 
 // One tile: the x-quads xb * blockDim.x + threadIdx.x of row (y, z), i.e.
 // cells [4 xb blockDim.x, 4 (xb + 1) blockDim.x). With STATS the block writes
@@ -278,7 +284,7 @@ __device__ __forceinline__ void quad_tile(const __half *src, __half *dst, const 
 // The step runs as an interior launch and a wall-row launch, so that the wall
 // layer's code does not shape the register allocation of the interior rows.
 template <bool STATS, int COLL = COLL_BGK, int ROWS = ROWS_ALL>
-__global__ void __launch_bounds__(128, LBM_QUAD_MIN_BLOCKS) k_step_quad(const __half *__restrict__ src,
+__global__ void __launch_bounds__(128, COLL == COLL_MRT ? LBM_QUAD_MRT_MIN_BLOCKS : LBM_QUAD_MIN_BLOCKS) k_step_quad(const __half *__restrict__ src,
                                                                          __half *__restrict__ dst, Geom g, Phys p,
                                                                          float *__restrict__ tw_out,
                                                                          double *__restrict__ part)
@@ -296,7 +302,7 @@ __global__ void __launch_bounds__(128, LBM_QUAD_MIN_BLOCKS) k_step_quad(const __
 // the row set ROWS (grid.y ny, or ny - 2 for the interior rows, row
 // blockIdx.y + 1).
 template <bool STATS, int COLL, int LAY, int ROWS = ROWS_ALL>
-__global__ void __launch_bounds__(128, LBM_QUAD_MIN_BLOCKS) k_step_quad_aa(__half *f, Geom g, Phys p,
+__global__ void __launch_bounds__(128, COLL == COLL_MRT ? LBM_QUAD_MRT_MIN_BLOCKS : LBM_QUAD_AA_MIN_BLOCKS) k_step_quad_aa(__half *f, Geom g, Phys p,
                                                                             float *__restrict__ tw_out,
                                                                             double *__restrict__ part)
 {

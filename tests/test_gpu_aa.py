@@ -126,7 +126,16 @@ def test_aa_statistics_and_mrt_match_pull(precision):
     (fa, sa, wa, na), (fb, sb, wb, nb) = res
     assert na == nb == 14
     assert np.array_equal(fa, fb)
-    assert np.array_equal(sa, sb)
+    if precision == lbm.FP32:
+        assert np.array_equal(sa, sb)
+    else:
+        # the two-lattice FP16 MRT step runs its wall rows in a second launch
+        # with the two-cell tile, whose blocks add the same FP64 cell terms in
+        # another order than the single AA launch: the plane sums agree to the
+        # rounding of that order (the cell values themselves are bitwise equal,
+        # as the populations show)
+        scale = np.max(np.abs(sa), axis=0)
+        assert np.all(np.abs(sa - sb) <= 1e-12 * scale), np.max(np.abs(sa - sb) / scale)
     # tau_w is FP32 arithmetic that the compiler may contract into FMAs
     # differently in two kernel instantiations; under FP16 storage the last-bit
     # difference does not reach the stored populations, only the wall sums
