@@ -40,9 +40,14 @@ SAMPLE_CELLS = 2_100_000      # cells of the bounded oracle sample (a z-slab of 
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # dominant kernel from one ncu capture of the current kernel build, keyed by
-# (workload, storage, layout); the captures are summarised under profiles/.
-# Absent keys report null.
-NCU_TRAFFIC = {}
+# (workload, storage, layout, collision); the captures are summarised under
+# profiles/. A workload too large for a multi-metric capture is captured as a
+# z-slab of the same channel and scaled by its cell count (traffic per cell
+# does not depend on nz). Absent keys report null.
+NCU_TRAFFIC = {
+    # k_step_pair<float>, 1024x256x16 slab: 598.4 MB per launch (142.7 B/cell) x 32
+    ("c4", "fp32", "pull", "bgk"): 19.149e9,
+}
 
 
 def parse(argv=None):
@@ -55,6 +60,9 @@ def parse(argv=None):
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16"])
     ap.add_argument("--layout", default="pull", choices=["pull", "aa"],
                     help="two-lattice pull (default) or the single-lattice AA layout")
+    ap.add_argument("--les", default="bgk", choices=["bgk", "mrt"],
+                    help="collision of the timed channel: BGK + Smagorinsky (default) or the paper's MRT + "
+                         "Smagorinsky + van Driest (A+ = 26)")
     ap.add_argument("--nz", type=int, default=0,
                     help="run a z-slab of the workload with this many planes (same nx, ny and parameters), "
                          "for bounded profiler captures; 0 runs the whole grid")
@@ -77,12 +85,12 @@ def headline_kernel(case, precision, layout=0):
 
 
 def launches_per_step(case, precision, layout=0, mrt=False):
-    """Step-kernel launches per step: the two-lattice FP16 four-cell form with
-    BGK runs an interior-row launch and a wall-row launch; every other form
-    one."""
+    """Step-kernel launches per step: the two-lattice FP16 four-cell form runs
+    an interior-row launch and a wall-row launch (BGK and MRT alike); every
+    other form one."""
     from paper_2009_04352_gb300 import lbm
     quad = precision == lbm.FP16_SHIFTED and case.nx % 4 == 0
-    return 2 if quad and layout == lbm.PULL2 and not mrt and case.ny > 2 else 1
+    return 2 if quad and layout == lbm.PULL2 and case.ny > 2 else 1
 
 
 def sample_case(case, cells=SAMPLE_CELLS):
@@ -496,7 +504,7 @@ def main():
 
     with ClockSampler(local) as clocks:
         ms, finite, (h0, h1) = time_channel(case, precision, args.steps, args.warmup, stream, layout=layout,
-                                            barrier=pg.barrier if pg else None)
+                                            mrt=args.les == "mrt", barrier=pg.barrier if pg else None)
         torch.cuda.synchronize()
         per_gpu_mlups = case.cells * args.steps / (ms * 1e-3) / 1e6
         mlups, ms, total_cells = whole_job_rate(case.cells, args.steps, ms, pg, "cuda")
@@ -532,7 +540,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": case.name, "grid": [case.nx, case.ny, case.nz], "cells": case.cells,
                    "re_tau": case.re_tau, "tau0": case.tau, "C_s": case.cs, "wall": "wfb",
-                   "storage": args.precision,
+                   "storage": args.precision, "les": "MRT + van Driest" if args.les == "mrt" else "BGK",
                    "layout": "single-lattice AA" if layout == lbm.AA else "two-lattice pull",
                    "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (129 MB): %s %.0f MB lattice%s per step" % (
@@ -540,12 +548,13 @@ def main():
                        "" if layout == lbm.AA else "s")},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
-                     "traffic": NCU_TRAFFIC.get((args.workload, args.precision, args.layout)),
+                     "traffic": NCU_TRAFFIC.get((args.workload, args.precision, args.layout, args.les))
+                     if args.nz == 0 else None,
                      "peak_source": peak_src, "kernel": headline_kernel(case, precision, layout),
                      "bytes_per_lup": BYTES_PER_LUP[precision],
                      "frac_nominal": achieved / NOMINAL_HBM_GBS, "nominal_peak": NOMINAL_HBM_GBS},
         "per_gpu_MLUPS": per_gpu_mlups, "finite": finite,
-        "gpu_launches": args.steps * launches_per_step(case, precision, layout),
+        "gpu_launches": args.steps * launches_per_step(case, precision, layout, args.les == "mrt"),
         "clocks": clocks.summary(h0, h1),
         "clocks_whole_run": clocks.summary(),
     }

@@ -233,6 +233,17 @@ int lbm_set_kernel(lbm_handle *h, int kernel);
 /* The kernel form in use (never LBM_KERNEL_AUTO), -1 for a NULL handle. */
 int lbm_get_kernel(lbm_handle *h);
 
+/* Tile-shape autotuner of a single channel (no counterpart in the paper): time
+ * every kernel form the grid allows (CELL, PAIR, TMA, QUAD: one, two or four
+ * cells per thread, or the row-pipelined CTA) for `steps` >= 1 steps each,
+ * after 2 warm-up steps and its graph build, with CUDA events on the handle's
+ * stream, and keep the fastest. best_ms and best_kernel (nullable) receive its
+ * time per step and its lbm_kernel value. The timed steps advance the state
+ * like lbm_step (all forms compute the same update), so the step count grows
+ * by (steps + 2) per form tried. Synchronises. Errors: LBM_ERR_ARG (NULL
+ * handle, steps < 1), LBM_ERR_STATE (batch member), LBM_ERR_CUDA. */
+int lbm_autotune(lbm_handle *h, int steps, double *best_ms, int *best_kernel);
+
 typedef enum {
     LBM_COLLISION_BGK = 0,  /* single relaxation time (default) */
     LBM_COLLISION_MRT = 1   /* D3Q19 multiple relaxation times (ref. [40] of Sec. 3.1) */

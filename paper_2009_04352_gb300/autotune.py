@@ -1,10 +1,12 @@
-"""Launch-shape autotuning of the batched ensemble, with a JSON cache.
+"""Launch-shape autotuning of single channels and of the batched ensemble,
+with a JSON cache.
 
-The timing itself runs in the library (lbm_batch_autotune tries both batch
+The timing itself runs in the library: lbm_autotune times every kernel form
+a channel's grid allows (one, two or four cells per thread, or the
+row-pipelined CTA) and keeps the fastest; lbm_batch_autotune tries both batch
 forms, the persistent kernel at every (threads per CTA, CTAs per SM) shape and
-the member grids on 4, 8 and 16 streams, and keeps the fastest); this module
-remembers the winner per (GPU, storage precision, member grids) so that later
-runs apply it without re-timing.
+the member grids on 4, 8 and 16 streams. This module remembers the winners
+per GPU and problem so that later runs apply them without re-timing.
 """
 from __future__ import annotations
 
@@ -33,6 +35,39 @@ def _load(path):
         return {}
 
 
+def channel_key(ch) -> str:
+    import torch
+    dev = torch.cuda.get_device_name(torch.cuda.current_device())
+    return (f"{dev}|channel|prec{ch.precision}|layout{ch.layout}|{ch.nx}x{ch.ny}x{ch.nz}|wall{ch.wall}"
+            f"|coll{ch.collision}")
+
+
+def tune_channel(ch, cache_path: str | None = None, steps: int = 16, retune: bool = False) -> dict:
+    """Apply the cached kernel form for this channel, or time every form and
+    cache the fastest. Timing advances the state, so call it before
+    initialising the channel. Returns {"kernel", "ms_per_step" (None if from
+    cache), "cached"}."""
+    path = cache_path or DEFAULT_CACHE
+    cache = _load(path)
+    key = channel_key(ch)
+    if key in cache and not retune:
+        ch.set_kernel(cache[key]["kernel"])
+        return {**cache[key], "cached": True}
+    kernel, ms = ch.autotune(steps)
+    cfg = {"kernel": kernel, "ms_per_step": ms}
+    _store(path, cache, key, cfg)
+    return {**cfg, "cached": False}
+
+
+def _store(path, cache, key, cfg):
+    cache[key] = cfg
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = f"{path}.tmp{os.getpid()}"
+    with open(tmp, "w") as fh:
+        json.dump(cache, fh, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
 def tune_batch(batch, cache_path: str | None = None, steps: int = 3, retune: bool = False) -> dict:
     """Apply the cached launch shape for this batch, or time all shapes and cache
     the fastest. Timing advances the members, so call it before initialising them.
@@ -49,10 +84,5 @@ def tune_batch(batch, cache_path: str | None = None, steps: int = 3, retune: boo
     c = batch.config()
     cfg = {"form": c["form"], "streams": c["streams"], "threads": c["threads"], "ctas_per_sm": c["ctas_per_sm"],
            "ms_per_step": ms}
-    cache[key] = cfg
-    os.makedirs(os.path.dirname(path), exist_ok=True)
-    tmp = f"{path}.tmp{os.getpid()}"
-    with open(tmp, "w") as fh:
-        json.dump(cache, fh, indent=1, sort_keys=True)
-    os.replace(tmp, path)
+    _store(path, cache, key, cfg)
     return {**cfg, "cached": False}

@@ -758,6 +758,46 @@ int lbm_set_kernel(lbm_handle *h, int kernel)
 
 int lbm_get_kernel(lbm_handle *h) { return h ? h->kernel : -1; }
 
+int lbm_autotune(lbm_handle *h, int steps, double *best_ms, int *best_kernel)
+{
+    LbmRange range("lbm_autotune");
+    if (!h || steps < 1) return fail(LBM_ERR_ARG, "invalid argument");
+    if (h->member) return fail(LBM_ERR_STATE, "a batch member is tuned through its batch");
+    CK(cudaStreamSynchronize(h->stream));
+    const int forms[4] = {LBM_KERNEL_CELL, LBM_KERNEL_PAIR, LBM_KERNEL_TMA, LBM_KERNEL_QUAD};
+    cudaEvent_t ev[2];
+    CK(cudaEventCreate(&ev[0]));
+    CK(cudaEventCreate(&ev[1]));
+    int best = -1, rc = LBM_OK;
+    float best_t = 0.f;
+    for (int i = 0; i < 4 && rc == LBM_OK; ++i) {
+        if (select_kernel(h, forms[i]) != LBM_OK) continue;   // the grid does not allow this form
+        rc = lbm_step(h, 2);                                     // builds the form's graphs
+        if (rc != LBM_OK) break;
+        float t = 0.f;
+        cudaError_t e = cudaEventRecord(ev[0], h->stream);
+        if (e == cudaSuccess) rc = lbm_step(h, steps);
+        if (e == cudaSuccess && rc == LBM_OK) e = cudaEventRecord(ev[1], h->stream);
+        if (e == cudaSuccess && rc == LBM_OK) e = cudaEventSynchronize(ev[1]);
+        if (e == cudaSuccess && rc == LBM_OK) e = cudaEventElapsedTime(&t, ev[0], ev[1]);
+        if (e != cudaSuccess) rc = fail(LBM_ERR_CUDA, "autotune timing: %s", cudaGetErrorString(e));
+        if (rc == LBM_OK) rc = check_err(h);
+        if (rc == LBM_OK && (best < 0 || t < best_t)) {
+            best = forms[i];
+            best_t = t;
+        }
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (rc != LBM_OK) return rc;
+    if (best < 0) return fail(LBM_ERR_ARG, "no kernel form applies to this grid");
+    rc = select_kernel(h, best);
+    if (rc != LBM_OK) return rc;
+    if (best_ms) *best_ms = best_t / steps;
+    if (best_kernel) *best_kernel = best;
+    return LBM_OK;
+}
+
 int lbm_set_les(lbm_handle *h, int collision, double u_tau_ref, double a_plus)
 {
     if (!h) return fail(LBM_ERR_ARG, "NULL handle");

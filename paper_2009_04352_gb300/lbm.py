@@ -77,6 +77,7 @@ _SIGNATURES = {
     "lbm_get_step": (C.c_longlong, [_VP]),
     "lbm_set_kernel": (C.c_int, [_VP, C.c_int]),
     "lbm_get_kernel": (C.c_int, [_VP]),
+    "lbm_autotune": (C.c_int, [_VP, C.c_int, _DP, C.POINTER(C.c_int)]),
     "lbm_set_les": (C.c_int, [_VP, C.c_int, C.c_double, C.c_double]),
     "lbm_moments": (C.c_int, [_VP, _VP, _VP, C.c_int]),
     "lbm_wall_stress": (C.c_int, [_VP, _VP, C.c_int]),
@@ -210,6 +211,14 @@ def lbm_get_kernel(h):
     return int(lib().lbm_get_kernel(h))
 
 
+def lbm_autotune(h, steps):
+    """Time every kernel form the grid allows and keep the fastest; returns
+    (kernel, ms per step)."""
+    ms, k = C.c_double(), C.c_int()
+    _check(lib().lbm_autotune(h, int(steps), C.byref(ms), C.byref(k)))
+    return int(k.value), float(ms.value)
+
+
 def lbm_set_les(h, collision, u_tau_ref=0.0, a_plus=0.0):
     _check(lib().lbm_set_les(h, int(collision), float(u_tau_ref), float(a_plus)))
 
@@ -261,7 +270,7 @@ class Channel:
                  newton_iters=12, precision=FP32, layout=PULL2, stream=None, law=LAW_SPALDING):
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         self.n = self.nx * self.ny * self.nz
-        self.precision = precision
+        self.precision, self.layout, self.wall, self.collision = precision, layout, wall, COLLISION_BGK
         self._h = lbm_create(nx, ny, nz, tau, cs, force, wall, kappa, B, y1, nu, newton_iters, precision,
                              layout, stream, law)
 
@@ -273,7 +282,8 @@ class Channel:
         self = cls.__new__(cls)
         self.nx, self.ny, self.nz = case.nx, case.ny, case.nz
         self.n = self.nx * self.ny * self.nz
-        self.precision = precision
+        self.precision, self.layout, self.collision = precision, layout, COLLISION_BGK
+        self.wall = case.wall if wall is None else wall
         need = lbm_population_bytes(case.nx, case.ny, case.nz, precision)
         for t in buffers:
             if not t.is_cuda or t.numel() * t.element_size() < need:
@@ -333,8 +343,14 @@ class Channel:
     def set_kernel(self, kernel):
         lbm_set_kernel(self._h, kernel)
 
+    def autotune(self, steps=16):
+        """Select the fastest kernel form for this grid (advances the state by
+        steps + 2 per form tried). Returns (kernel, ms per step)."""
+        return lbm_autotune(self._h, steps)
+
     def set_les(self, collision=COLLISION_BGK, u_tau_ref=0.0, a_plus=0.0):
         lbm_set_les(self._h, collision, u_tau_ref, a_plus)
+        self.collision = collision
 
     def moments(self, device=False):
         """(rho [nz,ny,nx], u [3,nz,ny,nx]) as FP32 numpy arrays, or torch CUDA

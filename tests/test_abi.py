@@ -120,9 +120,14 @@ def test_bench_launch_and_kernel_bookkeeping():
     assert bench.launches_per_step(c2, lbm.FP32) == 1
     assert bench.launches_per_step(c3, lbm.FP16_SHIFTED) == 2           # interior + wall rows
     assert bench.launches_per_step(c3, lbm.FP16_SHIFTED, lbm.AA) == 1
-    assert bench.launches_per_step(c3, lbm.FP16_SHIFTED, mrt=True) == 1
+    assert bench.launches_per_step(c3, lbm.FP16_SHIFTED, mrt=True) == 2   # MRT splits the same way
     assert bench.launches_per_step(c3.with_(ny=2), lbm.FP16_SHIFTED) == 1
     assert bench.headline_kernel(c2, lbm.FP32) == "k_step_pair"
     assert bench.headline_kernel(c3, lbm.FP16_SHIFTED) == "k_step_quad"
     assert bench.headline_kernel(c3, lbm.FP16_SHIFTED, lbm.AA) == "k_step_quad_aa"
     assert bench.headline_kernel(c2.with_(nx=37), lbm.FP32) == "k_step"
+
+
+def test_autotune_rejects_bad_arguments_without_device(built_lib):
+    from paper_2009_04352_gb300 import lbm
+    assert lbm.lib().lbm_autotune(None, 4, None, None) == lbm.LBM_ERR_ARG
