@@ -216,27 +216,13 @@ cudaError_t launch_aa(lbm_handle *h, cudaStream_t s, bool stats)
 {
     const dim3 grid = step_grid(h), block(h->bx);
     void *f = h->f[0];
-#ifndef LBM_QUAD_AA_SPLIT
-#define LBM_QUAD_AA_SPLIT 0   // 1: interior and wall-row launches (measured slower in place)
-#endif
     if (h->kernel == LBM_KERNEL_QUAD) {
+        // one launch over every row (an interior / wall-row split, as in the
+        // two-lattice step, measured slower for the in-place steps)
         __half *fh = (__half *)f;
-        if (!LBM_QUAD_AA_SPLIT || h->g.ny <= 2)
-            return stats ? launch_pdl(lbm::k_step_quad_aa<true, COLL, LAY>, grid, block, 0, s, fh, h->g, h->p, h->tw,
-                                      h->part)
-                         : launch_pdl(lbm::k_step_quad_aa<false, COLL, LAY>, grid, block, 0, s, fh, h->g, h->p, h->tw,
-                                      h->part);
-        // interior rows, then the two wall rows with the two-cell tile
-        const dim3 gi(grid.x, h->g.ny - 2, grid.z), gw(grid.x, 2, grid.z), bw(2 * h->bx);
-        cudaError_t e = stats ? launch_pdl(lbm::k_step_quad_aa<true, COLL, LAY, lbm::ROWS_INTERIOR>, gi, block, 0, s,
-                                           fh, h->g, h->p, h->tw, h->part)
-                              : launch_pdl(lbm::k_step_quad_aa<false, COLL, LAY, lbm::ROWS_INTERIOR>, gi, block, 0, s,
-                                           fh, h->g, h->p, h->tw, h->part);
-        if (e != cudaSuccess) return e;
-        return stats ? launch_pdl(lbm::k_step_pair_wall<__half, true, COLL, LAY>, gw, bw, 0, s, fh, fh, h->g, h->p,
-                                  h->tw, h->part)
-                     : launch_pdl(lbm::k_step_pair_wall<__half, false, COLL, LAY>, gw, bw, 0, s, fh, fh, h->g, h->p,
-                                  h->tw, h->part);
+        return stats ? launch_pdl(lbm::k_step_quad_aa<true, COLL, LAY>, grid, block, 0, s, fh, h->g, h->p, h->tw, h->part)
+                     : launch_pdl(lbm::k_step_quad_aa<false, COLL, LAY>, grid, block, 0, s, fh, h->g, h->p, h->tw,
+                                  h->part);
     }
     if (h->kernel == LBM_KERNEL_PAIR) {
         if (h->precision == LBM_FP16_SHIFTED) {

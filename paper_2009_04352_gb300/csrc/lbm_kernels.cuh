@@ -252,28 +252,90 @@ __device__ __forceinline__ void wall_layer(float (&fs)[Q], const CellState &c, c
     }
 }
 
-// Add one cell to the FP64 partial statistics (K_STATS plane sums, then the
-// wall sums tau_x, tau_z, |tau|, |tau|^2). Every rounding is explicit, so the
-// sums do not depend on how the compiler contracts them in a given kernel.
-__device__ __forceinline__ void accumulate_cell(double (&v)[K_PART], double r, double ux, double uy, double uz,
-                                                double tx, double tz)
+// Fused plane statistics of a sampled step. FP64 arithmetic runs at 1/64 of
+// the FP32 rate on this GPU, so a per-cell FP64 accumulation made a sampled
+// step several times slower than a plain one. The per-cell values are FP32
+// anyway; a thread adds its cells in FP32, the warp sums them in FP32 (a
+// tree of depth 5), and only the warp sums are converted: the block, plane and
+// time sums are FP64. K_ACC = the K_PART sums (rho kept as rho - 1, which is
+// exact, so that adding values near 1 loses nothing) and the cell count.
+constexpr int K_ACC = K_PART + 1;
+
+__device__ __forceinline__ void stats_zero(float (&v)[K_ACC])
 {
-    const double m2 = __fma_rn(tz, tz, __dmul_rn(tx, tx));
-    v[0] = __dadd_rn(v[0], r);
-    v[1] = __dadd_rn(v[1], ux);
-    v[2] = __dadd_rn(v[2], uy);
-    v[3] = __dadd_rn(v[3], uz);
-    v[4] = __fma_rn(ux, ux, v[4]);
-    v[5] = __fma_rn(uy, uy, v[5]);
-    v[6] = __fma_rn(uz, uz, v[6]);
-    v[7] = __fma_rn(ux, uy, v[7]);
-    v[8] = __fma_rn(r, ux, v[8]);
-    v[9] = __fma_rn(r, uy, v[9]);
-    v[10] = __fma_rn(r, uz, v[10]);
-    v[11] = __dadd_rn(v[11], tx);
-    v[12] = __dadd_rn(v[12], tz);
-    v[13] = __dadd_rn(v[13], __dsqrt_rn(m2));
-    v[14] = __dadd_rn(v[14], m2);
+#pragma unroll
+    for (int k = 0; k < K_ACC; ++k) v[k] = 0.f;
+}
+
+// Add one cell (K_STATS plane sums, then the wall sums tau_x, tau_z, |tau|,
+// |tau|^2 for a cell of a wall layer). Every rounding is explicit, so the sums
+// do not depend on how the compiler contracts them in a given kernel.
+__device__ __forceinline__ void stats_cell(float (&v)[K_ACC], float rho, float ux, float uy, float uz, float tx,
+                                           float tz, bool wall)
+{
+    const float dr = __fsub_rn(rho, 1.f);
+    v[0] = __fadd_rn(v[0], dr);
+    v[1] = __fadd_rn(v[1], ux);
+    v[2] = __fadd_rn(v[2], uy);
+    v[3] = __fadd_rn(v[3], uz);
+    v[4] = __fmaf_rn(ux, ux, v[4]);
+    v[5] = __fmaf_rn(uy, uy, v[5]);
+    v[6] = __fmaf_rn(uz, uz, v[6]);
+    v[7] = __fmaf_rn(ux, uy, v[7]);
+    v[8] = __fadd_rn(v[8], __fmul_rn(rho, ux));
+    v[9] = __fadd_rn(v[9], __fmul_rn(rho, uy));
+    v[10] = __fadd_rn(v[10], __fmul_rn(rho, uz));
+    if (wall) {
+        const float m2 = __fmaf_rn(tz, tz, __fmul_rn(tx, tx));
+        v[11] = __fadd_rn(v[11], tx);
+        v[12] = __fadd_rn(v[12], tz);
+        v[13] = __fadd_rn(v[13], __fsqrt_rn(m2));
+        v[14] = __fadd_rn(v[14], m2);
+    }
+    v[15] = __fadd_rn(v[15], 1.f);
+}
+
+// Sum the 16 accumulators over the warp by reduce-scatter: at the steps with
+// lane offsets 16, 8, 4 and 2 each lane keeps the half of its sums selected by
+// that bit of its lane index (8, 4, 2, 1 sums) and adds its partner's copy of
+// them; a last step adds the pair (lane, lane ^ 1). Lane L then holds the
+// warp's sum number L / 2 (16 shuffles and 16 adds per lane instead of 80).
+__device__ __forceinline__ float warp_stats_reduce(float (&v)[K_ACC])
+{
+    static_assert(K_ACC == 16, "the reduce-scatter splits 16 sums over 32 lanes");
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int h = 8, o = 16; h >= 1; h >>= 1, o >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const float send = up ? v[i] : v[i + h];
+            const float keep = up ? v[i + h] : v[i];
+            v[i] = __fadd_rn(keep, __shfl_xor_sync(0xffffffffu, send, o));
+        }
+    }
+    return __fadd_rn(v[0], __shfl_xor_sync(0xffffffffu, v[0], 1));
+}
+
+// Warp sums of the block's threads (FP32, warp_stats_reduce), added over the
+// warps in FP64 in a fixed order; writes the K_PART block sums to out
+// (rho as count + sum of rho - 1). All threads of the block must call it.
+__device__ __forceinline__ void stats_block_store(float (&v)[K_ACC], double *__restrict__ out)
+{
+    __shared__ double red[32][K_ACC];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const float w = warp_stats_reduce(v);
+    if (!(lane & 1)) red[warp][lane >> 1] = (double)w;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    if (threadIdx.x < K_PART) {
+        double s = 0.0;
+        for (int i = 0; i < nw; ++i) s += red[i][threadIdx.x];
+        if (threadIdx.x == 0)
+            for (int i = 0; i < nw; ++i) s += red[i][K_PART];
+        out[threadIdx.x] = s;
+    }
+    __syncthreads();   // red[] may be reused by the next call in the same block
 }
 
 template <int N>
@@ -383,12 +445,11 @@ __device__ __forceinline__ void cell_step(const T *src, T *dst, const Geom &g, c
         }
     }
     if (STATS) {
-        double v[K_PART];
-#pragma unroll
-        for (int k = 0; k < K_PART; ++k) v[k] = 0.0;
-        if (valid) accumulate_cell(v, c.rho, c.ux, c.uy, c.uz, twx, twz);
+        float v[K_ACC];
+        stats_zero(v);
+        if (valid) stats_cell(v, c.rho, c.ux, c.uy, c.uz, twx, twz, y == 0 || y == g.ny - 1);
         const long long blk = ((long long)y * g.nz + z) * gridDim.x + blockIdx.x;
-        block_reduce_store<K_PART>(v, part + blk * K_PART);
+        stats_block_store(v, part + blk * K_PART);
     }
 }
 

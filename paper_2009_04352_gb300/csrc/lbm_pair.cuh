@@ -605,17 +605,17 @@ __device__ __forceinline__ void pair_tile(const T *src, T *dst, const Geom &g, c
         for (int a = 0; a < Q; ++a) st2<T>(d + (LAY == LAY_AA_EVEN ? opp_of(a) : a) * g.plane, f[a]);
     }
     if (STATS) {
-        double v[K_PART];
-#pragma unroll
-        for (int k = 0; k < K_PART; ++k) v[k] = 0.0;
+        float v[K_ACC];
+        stats_zero(v);
         if (valid) {
+            const bool wall = ROWS != ROWS_INTERIOR && (y == 0 || y == g.ny - 1);
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                accumulate_cell(v, h ? c.rho.y : c.rho.x, h ? c.ux.y : c.ux.x, h ? c.uy.y : c.uy.x,
-                                h ? c.uz.y : c.uz.x, h ? twx.y : twx.x, h ? twz.y : twz.x);
+                stats_cell(v, h ? c.rho.y : c.rho.x, h ? c.ux.y : c.ux.x, h ? c.uy.y : c.uy.x, h ? c.uz.y : c.uz.x,
+                           h ? twx.y : twx.x, h ? twz.y : twz.x, wall);
             }
         }
-        block_reduce_store<K_PART>(v, part_blk);
+        stats_block_store(v, part_blk);
     }
 }
 

@@ -184,7 +184,7 @@ __device__ __forceinline__ void push_quad(__half *dst, const Geom &g, int wall, 
 // Collision (and wall layer) of one packed pair held in word H of the quad.
 template <int H, bool STATS, int COLL>
 __device__ __forceinline__ void quad_half(uint2 (&r)[Q], const Phys &p, float smag, bool wall_row, bool bottom,
-                                          float4 &tw, double (&v)[K_PART], bool valid)
+                                          float4 &tw, float (&v)[K_ACC], bool valid)
 {
     float2 f[Q];
 #pragma unroll
@@ -205,8 +205,8 @@ __device__ __forceinline__ void quad_half(uint2 (&r)[Q], const Phys &p, float sm
     if (STATS && valid) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            accumulate_cell(v, h ? c.rho.y : c.rho.x, h ? c.ux.y : c.ux.x, h ? c.uy.y : c.uy.x,
-                            h ? c.uz.y : c.uz.x, h ? twx.y : twx.x, h ? twz.y : twz.x);
+            stats_cell(v, h ? c.rho.y : c.rho.x, h ? c.ux.y : c.ux.x, h ? c.uy.y : c.uy.x, h ? c.uz.y : c.uz.x,
+                       h ? twx.y : twx.x, h ? twz.y : twz.x, wall_row);
         }
     }
 }
@@ -216,6 +216,9 @@ __device__ __forceinline__ void quad_half(uint2 (&r)[Q], const Phys &p, float sm
 #endif
 #ifndef LBM_QUAD_MRT_MIN_BLOCKS
 #define LBM_QUAD_MRT_MIN_BLOCKS 4   // the same for the MRT instantiations (128 registers)
+#endif
+#ifndef LBM_QUAD_STATS_MIN_BLOCKS
+#define LBM_QUAD_STATS_MIN_BLOCKS 4   // sampled steps (16 FP32 accumulators more): 128 registers
 #endif
 #ifndef LBM_QUAD_AA_MIN_BLOCKS
 #define LBM_QUAD_AA_MIN_BLOCKS 4    // the same for the in-place AA steps with BGK (128 registers)
@@ -228,31 +231,16 @@ __device__ __forceinline__ void quad_half(uint2 (&r)[Q], const Phys &p, float sm
 // every row, the interior rows 1 .. ny - 2 only (their instantiation carries
 // no wall-layer code), or the two wall rows only.
 
-template <bool STATS, int COLL = COLL_BGK, int LAY = LAY_PULL, int ROWS = ROWS_ALL>
-__device__ __forceinline__ void quad_tile(const __half *src, __half *dst, const Geom &g, const Phys &p,
-                                          float *__restrict__ tw_out, double *__restrict__ part_blk, int xb, int y,
-                                          int z)
+// Collision, wall layer, store (or AA push) and statistics of the quad whose
+// 19 populations the gather left in r (the part of a tile after its loads).
+template <bool STATS, int COLL, int LAY, int ROWS>
+__device__ __forceinline__ void quad_finish(uint2 (&r)[Q], __half *dst, const Geom &g, const Phys &p,
+                                            float *__restrict__ tw_out, double *__restrict__ part_blk, int x0, int xl,
+                                            bool valid, int y, int z, int zm, int zp, int lane)
 {
-    const int lane = threadIdx.x & 31;
-    const int x0 = 4 * (xb * blockDim.x + threadIdx.x);
-    const bool valid = x0 < g.nx;
-    const int xl = valid ? x0 : g.nx - 4;   // lanes past the row end read in bounds and store nothing
-    const int zm = z == 0 ? g.nz - 1 : z - 1, zp = z == g.nz - 1 ? 0 : z + 1;
-
-    uint2 r[Q];
-    if (ROWS != ROWS_INTERIOR && y == 0)
-        gather_quad<ROW_BOTTOM, LAY>(src, g, p.wall, xl, y, z, zm, zp, lane, r);
-    else if (ROWS != ROWS_INTERIOR && y == g.ny - 1)
-        gather_quad<ROW_TOP, LAY>(src, g, p.wall, xl, y, z, zm, zp, lane, r);
-    else
-        gather_quad<ROW_INTERIOR, LAY>(src, g, p.wall, xl, y, z, zm, zp, lane, r);
-
     const bool wall_row = ROWS == ROWS_INTERIOR ? false : (ROWS == ROWS_WALL ? true : (y == 0 || y == g.ny - 1));
-    double v[K_PART];
-    if (STATS) {
-#pragma unroll
-        for (int k = 0; k < K_PART; ++k) v[k] = 0.0;
-    }
+    float v[K_ACC];
+    if (STATS) stats_zero(v);
     float4 twa = make_float4(0.f, 0.f, 0.f, 0.f), twb = twa;
     const float smag = row_smag(p, y, g.ny);
     quad_half<0, STATS, COLL>(r, p, smag, wall_row, y == 0, twa, v, valid);
@@ -276,7 +264,28 @@ __device__ __forceinline__ void quad_tile(const __half *src, __half *dst, const 
         for (int a = 0; a < Q; ++a)
             *reinterpret_cast<uint2 *>(d + (LAY == LAY_AA_EVEN ? opp_of(a) : a) * g.plane) = r[a];
     }
-    if (STATS) block_reduce_store<K_PART>(v, part_blk);
+    if (STATS) stats_block_store(v, part_blk);
+}
+
+template <bool STATS, int COLL = COLL_BGK, int LAY = LAY_PULL, int ROWS = ROWS_ALL>
+__device__ __forceinline__ void quad_tile(const __half *src, __half *dst, const Geom &g, const Phys &p,
+                                          float *__restrict__ tw_out, double *__restrict__ part_blk, int xb, int y,
+                                          int z)
+{
+    const int lane = threadIdx.x & 31;
+    const int x0 = 4 * (xb * blockDim.x + threadIdx.x);
+    const bool valid = x0 < g.nx;
+    const int xl = valid ? x0 : g.nx - 4;   // lanes past the row end read in bounds and store nothing
+    const int zm = z == 0 ? g.nz - 1 : z - 1, zp = z == g.nz - 1 ? 0 : z + 1;
+
+    uint2 r[Q];
+    if (ROWS != ROWS_INTERIOR && y == 0)
+        gather_quad<ROW_BOTTOM, LAY>(src, g, p.wall, xl, y, z, zm, zp, lane, r);
+    else if (ROWS != ROWS_INTERIOR && y == g.ny - 1)
+        gather_quad<ROW_TOP, LAY>(src, g, p.wall, xl, y, z, zm, zp, lane, r);
+    else
+        gather_quad<ROW_INTERIOR, LAY>(src, g, p.wall, xl, y, z, zm, zp, lane, r);
+    quad_finish<STATS, COLL, LAY, ROWS>(r, dst, g, p, tw_out, part_blk, x0, xl, valid, y, z, zm, zp, lane);
 }
 
 // The two-lattice step over the row set ROWS: grid.y is ny (ROWS_ALL), ny - 2
@@ -284,7 +293,9 @@ __device__ __forceinline__ void quad_tile(const __half *src, __half *dst, const 
 // The step runs as an interior launch and a wall-row launch, so that the wall
 // layer's code does not shape the register allocation of the interior rows.
 template <bool STATS, int COLL = COLL_BGK, int ROWS = ROWS_ALL>
-__global__ void __launch_bounds__(128, COLL == COLL_MRT ? LBM_QUAD_MRT_MIN_BLOCKS : LBM_QUAD_MIN_BLOCKS) k_step_quad(const __half *__restrict__ src,
+__global__ void __launch_bounds__(128, COLL == COLL_MRT ? LBM_QUAD_MRT_MIN_BLOCKS
+                                                         : (STATS ? LBM_QUAD_STATS_MIN_BLOCKS : LBM_QUAD_MIN_BLOCKS))
+    k_step_quad(const __half *__restrict__ src,
                                                                          __half *__restrict__ dst, Geom g, Phys p,
                                                                          float *__restrict__ tw_out,
                                                                          double *__restrict__ part)
@@ -302,7 +313,9 @@ __global__ void __launch_bounds__(128, COLL == COLL_MRT ? LBM_QUAD_MRT_MIN_BLOCK
 // the row set ROWS (grid.y ny, or ny - 2 for the interior rows, row
 // blockIdx.y + 1).
 template <bool STATS, int COLL, int LAY, int ROWS = ROWS_ALL>
-__global__ void __launch_bounds__(128, COLL == COLL_MRT ? LBM_QUAD_MRT_MIN_BLOCKS : LBM_QUAD_AA_MIN_BLOCKS) k_step_quad_aa(__half *f, Geom g, Phys p,
+__global__ void __launch_bounds__(128, COLL == COLL_MRT ? LBM_QUAD_MRT_MIN_BLOCKS
+                                                         : (STATS ? LBM_QUAD_STATS_MIN_BLOCKS : LBM_QUAD_AA_MIN_BLOCKS))
+    k_step_quad_aa(__half *f, Geom g, Phys p,
                                                                             float *__restrict__ tw_out,
                                                                             double *__restrict__ part)
 {

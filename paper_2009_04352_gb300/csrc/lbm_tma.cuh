@@ -207,11 +207,8 @@ __global__ void __launch_bounds__(NW * 32, 16 / NW) k_step_rows(const T *__restr
         const int y = (int)(r % g.ny), z = (int)(r / g.ny);
         const bool wall_row = y == 0 || y == g.ny - 1;
         const T *stage = ring + st * stage_elems;
-        double v[K_PART];
-        if (STATS) {
-#pragma unroll
-            for (int k = 0; k < K_PART; ++k) v[k] = 0.0;
-        }
+        float v[K_ACC];
+        if (STATS) stats_zero(v);
         for (int x0 = 2 * (warp * 32 + lane); x0 < g.nx; x0 += 64 * NW) {
             float2 f[Q];
             read_rows<T>(stage, g.nx, p.wall, y, g.ny, x0, f);
@@ -239,26 +236,21 @@ __global__ void __launch_bounds__(NW * 32, 16 / NW) k_step_rows(const T *__restr
             if (STATS) {
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    accumulate_cell(v, h ? c.rho.y : c.rho.x, h ? c.ux.y : c.ux.x, h ? c.uy.y : c.uy.x,
-                                    h ? c.uz.y : c.uz.x, h ? twx.y : twx.x, h ? twz.y : twz.x);
+                    stats_cell(v, h ? c.rho.y : c.rho.x, h ? c.ux.y : c.ux.x, h ? c.uy.y : c.uy.x,
+                               h ? c.uz.y : c.uz.x, h ? twx.y : twx.x, h ? twz.y : twz.x, wall_row);
                 }
             }
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_addr(empty + st));
         if (STATS) {
-#pragma unroll
-            for (int k = 0; k < K_PART; ++k) {
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
-            }
-            if (lane < K_PART) {
-                double mine_v = 0.0;
-#pragma unroll
-                for (int k = 0; k < K_PART; ++k)
-                    if (lane == k) mine_v = v[k];
-                part[(((long long)y * g.nz + z) * NW + warp) * K_PART + lane] = mine_v;
-            }
+            // warp sums in FP32 (stats_block_store of lbm_kernels.cuh explains
+            // why); lane 2k holds sum k, lane 30 the cell count
+            const float w = warp_stats_reduce(v);
+            const float cnt = __shfl_sync(0xffffffffu, w, 2 * K_PART);
+            if (!(lane & 1) && (lane >> 1) < K_PART)
+                part[(((long long)y * g.nz + z) * NW + warp) * K_PART + (lane >> 1)] =
+                    lane == 0 ? (double)w + (double)cnt : (double)w;
         }
     }
 }

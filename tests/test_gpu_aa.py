@@ -130,16 +130,18 @@ def test_aa_statistics_and_mrt_match_pull(precision):
         assert np.array_equal(sa, sb)
     else:
         # the two-lattice FP16 MRT step runs its wall rows in a second launch
-        # with the two-cell tile, whose blocks add the same FP64 cell terms in
-        # another order than the single AA launch: the plane sums agree to the
-        # rounding of that order (the cell values themselves are bitwise equal,
-        # as the populations show)
+        # with the two-cell tile, whose threads and warps add the same cell
+        # values (bitwise equal, as the populations show) in another order
+        # than the single AA launch; the warp sums are FP32, so the plane sums
+        # agree to a few FP32 roundings of the warp sums
         scale = np.max(np.abs(sa), axis=0)
-        assert np.all(np.abs(sa - sb) <= 1e-12 * scale), np.max(np.abs(sa - sb) / scale)
+        assert np.all(np.abs(sa - sb) <= 1e-6 * scale), np.max(np.abs(sa - sb) / scale)
     # tau_w is FP32 arithmetic that the compiler may contract into FMAs
     # differently in two kernel instantiations; under FP16 storage the last-bit
-    # difference does not reach the stored populations, only the wall sums
-    assert np.allclose(wa, wb, rtol=1e-7, atol=0)
+    # difference does not reach the stored populations, only the wall sums,
+    # which the FP16 step also adds in another order (see above)
+    scale = np.max(np.abs(wa), axis=0)
+    assert np.all(np.abs(wa - wb) <= 1e-6 * scale), np.max(np.abs(wa - wb) / scale)
 
 
 def test_aa_set_populations_at_odd_phase():

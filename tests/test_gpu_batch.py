@@ -54,9 +54,13 @@ def test_batch_members_equal_single_channels(precision):
         sb, wb, nb = b.members[i].plane_stats()
         sc, wc, nc = ch.plane_stats()
         assert nb == nc == 14
-        # the FP64 reductions may sum in another order (tiles of another width)
-        assert np.allclose(sb, sc, rtol=1e-12, atol=1e-12 * np.max(np.abs(sc)))
-        assert np.allclose(wb, wc, rtol=1e-12, atol=1e-12 * np.max(np.abs(wc)))
+        # the members run the kernel their grid selects (four cells per thread
+        # for FP16 where nx allows): the same cell values, added per thread and
+        # per warp in FP32 in another order than the two-cell tiles, so the
+        # sums agree to a few FP32 roundings of the warp sums
+        for got, ref in ((sb, sc), (wb, wc)):
+            scale = np.max(np.abs(ref), axis=0)
+            assert np.all(np.abs(got - ref) <= 1e-6 * scale), np.max(np.abs(got - ref) / scale)
         ch.close()
     b.close()
 

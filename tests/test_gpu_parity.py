@@ -265,9 +265,13 @@ def test_quad_and_pair_kernels_agree_bitwise():
     sa, wa, na = a.plane_stats()
     sb, wb, nb = b.plane_stats()
     assert na == nb == 10
-    assert np.allclose(sa, sb, rtol=1e-12, atol=1e-12 * np.max(np.abs(sb)))
-    # the FP32 wall stress of a sampled step may differ in its last bit between
-    # the two forms (FP16 storage of the populations hides it)
-    assert np.allclose(wa, wb, rtol=1e-7, atol=1e-7 * np.max(np.abs(wb)))
+    # the plane sums add the same cell values per thread and warp in FP32 in
+    # another grouping (four against two cells per thread), and the FP32 wall
+    # stress of a sampled step may differ in its last bit between the two forms
+    # (FP16 storage of the populations hides it): they agree to a few FP32
+    # roundings of the warp sums
+    for got, ref in ((sa, sb), (wa, wb)):
+        scale = np.max(np.abs(ref), axis=0)
+        assert np.all(np.abs(got - ref) <= 1e-6 * scale), np.max(np.abs(got - ref) / scale)
     a.close()
     b.close()
