@@ -105,21 +105,24 @@ __device__ __forceinline__ CellState collide(const float (&f)[Q], float (&fs)[Q]
         ge_rest = fmaf(-30.f, ce, 12.f * cp);
         const float kq = fmaf(omega, p.mrt_a[MRT_Q], p.mrt_b[MRT_Q]);
         const float km = fmaf(omega, p.mrt_a[MRT_M], p.mrt_b[MRT_M]);
-        const float qx = kq * (((hd[3] + hd[4]) + (hd[6] + hd[7])) - 2.f * hd[0]);
-        const float qy = kq * (((hd[3] + hd[5]) + (hd[8] - hd[6])) - 2.f * hd[1]);
-        const float qz = kq * (((hd[4] + hd[5]) - (hd[7] + hd[8])) - 2.f * hd[2]);
-        const float mx = km * ((hd[3] + hd[6]) - (hd[4] + hd[7]));
-        const float my = km * (((hd[5] + hd[6]) + hd[8]) - hd[3]);
-        const float mz = km * ((hd[4] + hd[8]) - (hd[5] + hd[7]));
+        const float sxa = hd[3] + hd[6], sxb = hd[4] + hd[7];
+        const float sya = hd[5] + hd[8], syb = hd[3] - hd[6];
+        const float sza = hd[4] - hd[7], szb = hd[5] - hd[8];
+        const float qx = kq * fmaf(-2.f, hd[0], sxa + sxb);
+        const float qy = kq * fmaf(-2.f, hd[1], sya + syb);
+        const float qz = kq * fmaf(-2.f, hd[2], sza + szb);
+        const float mx = km * (sxa - sxb), my = km * (sya - syb), mz = km * (sza - szb);
+        const float t36a = qx + mx, t36b = qy - my, t47a = qx - mx, t47b = qz + mz, t58a = qy + my,
+                    t58b = qz - mz;
         go[0] = -4.f * qx;
         go[1] = -4.f * qy;
         go[2] = -4.f * qz;
-        go[3] = (qx + qy) + (mx - my);
-        go[4] = (qx + qz) + (mz - mx);
-        go[5] = (qy + qz) + (my - mz);
-        go[6] = (qx - qy) + (mx + my);
-        go[7] = (qx - qz) - (mx + mz);
-        go[8] = (qy - qz) + (my + mz);
+        go[3] = t36a + t36b;
+        go[4] = t47a + t47b;
+        go[5] = t58a + t58b;
+        go[6] = t36a - t36b;
+        go[7] = t47a - t47b;
+        go[8] = t58a - t58b;
     }
     // BGK (see the comment above the struct): weights scaled by 36, o36 = omega / 36
     const float S0 = fmaf(-1.5f, rho * usq, m.drho);   // isotropic part of (f^eq - w) / w

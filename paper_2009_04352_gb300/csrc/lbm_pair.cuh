@@ -237,7 +237,8 @@ __device__ __forceinline__ void wall_layer_pair(float2 (&f)[Q], const PairState 
 // the sum of phi_i C_i over q and m for its first member.
 struct MrtPair {
     float2 ea, ed, er;     // half-sum change of an axis / diagonal pair, change of the rest population
-    float2 cq[3], cm[3];   // C of q_x, q_y, q_z and m_x, m_y, m_z
+    float2 cq[3];          // C of q_x, q_y, q_z (axis pairs: half difference -4 C_q)
+    float2 od[6];          // half-difference change of the diagonal pairs 3 .. 8
 };
 
 __device__ __forceinline__ MrtPair mrt_ghost_pair(const float2 (&hs)[9], const float2 (&hd)[9], float2 f0,
@@ -256,30 +257,33 @@ __device__ __forceinline__ MrtPair mrt_ghost_pair(const float2 (&hs)[9], const f
     m.ea = fma2(bc(-11.f), ce, mul2(bc(-4.f), cp));
     m.ed = fma2(bc(8.f), ce, cp);
     m.er = fma2(bc(-30.f), ce, mul2(bc(12.f), cp));
-    // pairs 3..8: first members (1,1,0), (1,0,1), (0,1,1), (1,-1,0), (1,0,-1), (0,1,-1)
-    m.cq[0] = mul2(kq, sub2(add2(add2(hd[3], hd[4]), add2(hd[6], hd[7])), add2(hd[0], hd[0])));
-    m.cq[1] = mul2(kq, sub2(add2(add2(hd[3], hd[5]), sub2(hd[8], hd[6])), add2(hd[1], hd[1])));
-    m.cq[2] = mul2(kq, sub2(sub2(add2(hd[4], hd[5]), add2(hd[7], hd[8])), add2(hd[2], hd[2])));
-    m.cm[0] = mul2(km, sub2(add2(hd[3], hd[6]), add2(hd[4], hd[7])));
-    m.cm[1] = mul2(km, sub2(add2(add2(hd[5], hd[6]), hd[8]), hd[3]));
-    m.cm[2] = mul2(km, sub2(add2(hd[4], hd[8]), add2(hd[5], hd[7])));
+    // pairs 3..8: first members (1,1,0), (1,0,1), (0,1,1), (1,-1,0), (1,0,-1),
+    // (0,1,-1); the q and m brackets share their partial sums
+    const float2 sxa = add2(hd[3], hd[6]), sxb = add2(hd[4], hd[7]);   // q_x = sxa + sxb - 2 hd_x, m_x = sxa - sxb
+    const float2 sya = add2(hd[5], hd[8]), syb = sub2(hd[3], hd[6]);   // q_y = sya + syb - 2 hd_y, m_y = sya - syb
+    const float2 sza = sub2(hd[4], hd[7]), szb = sub2(hd[5], hd[8]);   // q_z = sza + szb - 2 hd_z, m_z = sza - szb
+    m.cq[0] = mul2(kq, fma2(bc(-2.f), hd[0], add2(sxa, sxb)));
+    m.cq[1] = mul2(kq, fma2(bc(-2.f), hd[1], add2(sya, syb)));
+    m.cq[2] = mul2(kq, fma2(bc(-2.f), hd[2], add2(sza, szb)));
+    const float2 cmx = mul2(km, sub2(sxa, sxb)), cmy = mul2(km, sub2(sya, syb)), cmz = mul2(km, sub2(sza, szb));
+    // pair 3 / 6: (Cq_x + Cm_x) +/- (Cq_y - Cm_y); 4 / 7: (Cq_x - Cm_x) +/- (Cq_z + Cm_z);
+    // 5 / 8: (Cq_y + Cm_y) +/- (Cq_z - Cm_z)
+    const float2 t36a = add2(m.cq[0], cmx), t36b = sub2(m.cq[1], cmy);
+    const float2 t47a = sub2(m.cq[0], cmx), t47b = add2(m.cq[2], cmz);
+    const float2 t58a = add2(m.cq[1], cmy), t58b = sub2(m.cq[2], cmz);
+    m.od[0] = add2(t36a, t36b);
+    m.od[3] = sub2(t36a, t36b);
+    m.od[1] = add2(t47a, t47b);
+    m.od[4] = sub2(t47a, t47b);
+    m.od[2] = add2(t58a, t58b);
+    m.od[5] = sub2(t58a, t58b);
     return m;
 }
 
 // dd + the half-difference change of pair k from the q and m corrections.
 __device__ __forceinline__ float2 mrt_odd_add(const MrtPair &m, int k, float2 dd)
 {
-    switch (k) {
-    case 0: return fma2(bc(-4.f), m.cq[0], dd);
-    case 1: return fma2(bc(-4.f), m.cq[1], dd);
-    case 2: return fma2(bc(-4.f), m.cq[2], dd);
-    case 3: return add2(dd, add2(add2(m.cq[0], m.cq[1]), sub2(m.cm[0], m.cm[1])));
-    case 4: return add2(dd, add2(add2(m.cq[0], m.cq[2]), sub2(m.cm[2], m.cm[0])));
-    case 5: return add2(dd, add2(add2(m.cq[1], m.cq[2]), sub2(m.cm[1], m.cm[2])));
-    case 6: return add2(dd, add2(sub2(m.cq[0], m.cq[1]), add2(m.cm[0], m.cm[1])));
-    case 7: return add2(dd, sub2(sub2(m.cq[0], m.cq[2]), add2(m.cm[0], m.cm[2])));
-    default: return add2(dd, add2(sub2(m.cq[1], m.cq[2]), add2(m.cm[1], m.cm[2])));
-    }
+    return k < 3 ? fma2(bc(-4.f), m.cq[k], dd) : add2(dd, m.od[k - 3]);
 }
 
 // collide() of lbm_kernels.cuh for two cells (in place: f becomes f*),
