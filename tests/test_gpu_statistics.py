@@ -23,6 +23,7 @@ import pytest
 
 import oracle
 from paper_2009_04352_gb300 import lbm, workload
+from parity import _log
 
 pytestmark = pytest.mark.gpu
 
@@ -135,7 +136,11 @@ def test_long_chaotic_run_statistics_match_oracle(_cuda, precision):
         ux_o, uu_o, w_o = _window(P_o, W_o, n_o, cells, lo, hi)
         ux_g, uu_g, w_g = _window(P_g, W_g, n_g, cells, lo, hi)
         up_o, up_g = ux_o / u_tau, ux_g / u_tau
-        assert np.max(np.abs(up_g - up_o)) <= 0.01 * np.max(np.abs(up_o)), (lo, hi)
-        assert np.max(np.abs(w_g - w_o) / np.abs(w_o)) <= 0.01, (lo, hi, w_g, w_o)
+        err = {"u+": float(np.max(np.abs(up_g - up_o)) / np.max(np.abs(up_o))),
+               "tau_w": float(np.max(np.abs(w_g - w_o) / np.abs(w_o))),
+               "uu": float(np.max(np.abs(uu_g - uu_o)) / np.max(uu_o))}
+        _log(("c2 long run", lo, hi), precision, err, {})
+        assert err["u+"] <= 0.01, (lo, hi, err)
+        assert err["tau_w"] <= 0.01, (lo, hi, err, w_g, w_o)
         if precision == lbm.FP32:
-            assert np.max(np.abs(uu_g - uu_o)) <= 0.01 * np.max(uu_o), (lo, hi)
+            assert err["uu"] <= 0.01, (lo, hi, err)
