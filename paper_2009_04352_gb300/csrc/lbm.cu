@@ -276,33 +276,39 @@ int launch_step_c(lbm_handle *h, cudaStream_t s, int src, bool stats)
                 launch_rows_t<float, 4, COLL>(h, s, src, stats);
         }
     } else if (h->kernel == LBM_KERNEL_QUAD) {
-        // BGK: interior rows, then the two wall rows (the wall layer lives only
-        // in the second instantiation); MRT: one launch over every row (its
-        // interior-only instantiation spills more than the combined one)
+        // BGK: the interior rows, then the two wall rows with the two-cell tile
+        // in CTAs of twice the threads (the wall layer lives only in the second
+        // launch); MRT: one launch whose wall-row CTAs call a separately
+        // compiled wall tile (k_step_quad_rows), measured 1-2% faster for MRT
+        // and 8% slower for BGK than the two launches
         const __half *ah = (const __half *)a;
         __half *bh = (__half *)b;
-#ifndef LBM_QUAD_MRT_SPLIT
-#define LBM_QUAD_MRT_SPLIT 1
-#endif
-        if (COLL != lbm::COLL_BGK && !LBM_QUAD_MRT_SPLIT) {
-            e = stats ? launch_pdl(lbm::k_step_quad<true, COLL, lbm::ROWS_ALL>, grid, block, 0, s, ah, bh, h->g,
-                                   h->p, h->tw, h->part)
-                      : launch_pdl(lbm::k_step_quad<false, COLL, lbm::ROWS_ALL>, grid, block, 0, s, ah, bh, h->g,
-                                   h->p, h->tw, h->part);
-        } else if (h->g.ny > 2) {
-            const dim3 gi(grid.x, h->g.ny - 2, grid.z);
-            e = stats ? launch_pdl(lbm::k_step_quad<true, COLL, lbm::ROWS_INTERIOR>, gi, block, 0, s, ah, bh, h->g,
-                                   h->p, h->tw, h->part)
-                      : launch_pdl(lbm::k_step_quad<false, COLL, lbm::ROWS_INTERIOR>, gi, block, 0, s, ah, bh, h->g,
-                                   h->p, h->tw, h->part);
+        bool fused = false;
+        if constexpr (COLL == lbm::COLL_MRT) {
+            fused = h->g.ny > 2;
+            if (fused)
+                e = stats ? launch_pdl(lbm::k_step_quad_rows<true, COLL>, grid, block, 0, s, ah, bh, h->g, h->p,
+                                       h->tw, h->part)
+                          : launch_pdl(lbm::k_step_quad_rows<false, COLL>, grid, block, 0, s, ah, bh, h->g, h->p,
+                                       h->tw, h->part);
         }
-        // the wall rows with the two-cell tile in CTAs of twice the threads
-        const dim3 gw(grid.x, 2, grid.z), bw(2 * h->bx);
-        if ((COLL == lbm::COLL_BGK || LBM_QUAD_MRT_SPLIT) && e == cudaSuccess)
-            e = stats ? launch_pdl(lbm::k_step_pair_wall<__half, true, COLL>, gw, bw, 0, s, ah, bh, h->g, h->p, h->tw,
-                                   h->part)
-                      : launch_pdl(lbm::k_step_pair_wall<__half, false, COLL>, gw, bw, 0, s, ah, bh, h->g, h->p, h->tw,
-                                   h->part);
+        if (!fused) {
+            if constexpr (COLL == lbm::COLL_BGK) {
+                if (h->g.ny > 2) {
+                    const dim3 gi(grid.x, h->g.ny - 2, grid.z);
+                    e = stats ? launch_pdl(lbm::k_step_quad<true, COLL, lbm::ROWS_INTERIOR>, gi, block, 0, s, ah, bh,
+                                           h->g, h->p, h->tw, h->part)
+                              : launch_pdl(lbm::k_step_quad<false, COLL, lbm::ROWS_INTERIOR>, gi, block, 0, s, ah,
+                                           bh, h->g, h->p, h->tw, h->part);
+                }
+            }
+            const dim3 gw(grid.x, 2, grid.z), bw(2 * h->bx);
+            if (e == cudaSuccess)
+                e = stats ? launch_pdl(lbm::k_step_pair_wall<__half, true, COLL>, gw, bw, 0, s, ah, bh, h->g, h->p,
+                                       h->tw, h->part)
+                          : launch_pdl(lbm::k_step_pair_wall<__half, false, COLL>, gw, bw, 0, s, ah, bh, h->g, h->p,
+                                       h->tw, h->part);
+        }
     } else if (h->kernel == LBM_KERNEL_PAIR) {
         if (half) {
             const __half *ah = (const __half *)a;

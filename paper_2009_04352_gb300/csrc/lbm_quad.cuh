@@ -309,6 +309,36 @@ __global__ void __launch_bounds__(128, COLL == COLL_MRT ? LBM_QUAD_MRT_MIN_BLOCK
                                            blockIdx.x, y, z);
 }
 
+// The wall-row tile of the two-lattice four-cell step as a separate function:
+// called from k_step_quad_rows, it is compiled apart from the interior tile,
+// so the wall layer's code does not shape the interior's register allocation.
+template <bool STATS, int COLL>
+__device__ __noinline__ void quad_wall_tile(const __half *src, __half *dst, const Geom &g, const Phys &p,
+                                            float *tw_out, double *part_blk, int xb, int y, int z)
+{
+    quad_tile<STATS, COLL, LAY_PULL, ROWS_WALL>(src, dst, g, p, tw_out, part_blk, xb, y, z);
+}
+
+// The two-lattice four-cell step over every row in one launch: rows 1 .. ny - 2
+// run the interior tile inline, rows 0 and ny - 1 call quad_wall_tile. Unlike a
+// separate wall-row launch, the wall rows' CTAs (Newton iterations of the wall
+// law) overlap with the interior ones instead of running after them.
+template <bool STATS, int COLL>
+__global__ void __launch_bounds__(128, COLL == COLL_MRT ? LBM_QUAD_MRT_MIN_BLOCKS
+                                                         : (STATS ? LBM_QUAD_STATS_MIN_BLOCKS : LBM_QUAD_MIN_BLOCKS))
+    k_step_quad_rows(const __half *__restrict__ src, __half *__restrict__ dst, Geom g, Phys p,
+                     float *__restrict__ tw_out, double *__restrict__ part)
+{
+    pdl_begin();
+    const int y = blockIdx.y, z = blockIdx.z;
+    const long long blk = ((long long)y * g.nz + z) * gridDim.x + blockIdx.x;
+    double *pb = STATS ? part + blk * K_PART : nullptr;
+    if (y == 0 || y == g.ny - 1)
+        quad_wall_tile<STATS, COLL>(src, dst, g, p, tw_out, pb, blockIdx.x, y, z);
+    else
+        quad_tile<STATS, COLL, LAY_PULL, ROWS_INTERIOR>(src, dst, g, p, tw_out, pb, blockIdx.x, y, z);
+}
+
 // The four-cell step on the single AA array (LAY_AA_EVEN or LAY_AA_ODD) over
 // the row set ROWS (grid.y ny, or ny - 2 for the interior rows, row
 // blockIdx.y + 1).
