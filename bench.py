@@ -407,6 +407,19 @@ def cpu_model():
     return "unknown"
 
 
+def line_config(case, args, world):
+    """The workload of the line (the same dict for both arms)."""
+    aa = args.layout == "aa"
+    return {"workload": case.name, "grid": [case.nx, case.ny, case.nz], "cells": case.cells,
+            "re_tau": case.re_tau, "tau0": case.tau, "C_s": case.cs, "wall": "wfb",
+            "storage": args.precision, "les": "MRT + van Driest" if args.les == "mrt" else "BGK",
+            "layout": "single-lattice AA" if aa else "two-lattice pull",
+            "parallelism": f"replicas x{world}",
+            "l2": "inputs larger than L2 (129 MB): %s %.0f MB lattice%s per step" % (
+                "one" if aa else "two", BYTES_PER_LUP[0 if args.precision == "fp32" else 1] / 2 * case.cells / 1e6,
+                "" if aa else "s")}
+
+
 def main_reference(args):
     """The oracle on the host cores, each step a bounded sample of the
     workload (one oracle step of its z-slab)."""
@@ -414,10 +427,14 @@ def main_reference(args):
     if rank != 0:
         return 0
     case = workload.CASES[args.workload]
+    if args.nz > 0:
+        case = case.with_(nz=args.nz, name=f"{case.name}_zslab{args.nz}")
     s = sample_case(case)
     import oracle
     L = oracle.Lattice.from_case(s)
     threads = L.set_threads(os.cpu_count() or 1)
+    if args.les == "mrt":
+        L.set_les(1, case.u_tau, 26.0)
     L.init_channel(workload.u_mean_profile(s), workload.noise_amplitude(s), s.seed)
     L.step(max(0, args.warmup))
     steps = max(1, args.steps)
@@ -429,8 +446,7 @@ def main_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "MLUPS", "n_gpus": args.gpus,
             "steps": steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": case.name, "cells": case.cells,
-                                            "sample_cells": s.cells},
+            "data": "synthetic", "config": line_config(case, args, world),
             "cpu_baseline": {"value": val, "unit": "MLUPS", "cores": threads, "kind": "oracle",
                              "sample": f"FP64 oracle, each step one step of the {s.nx}x{s.ny}x{s.nz} z-slab of "
                                        f"{case.name} over {threads} threads (cpu: {cpu_model()})"},
@@ -539,14 +555,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": kernel_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if precision == lbm.FP32 else "f32 (fp16 storage)",
         "data": "synthetic",
-        "config": {"workload": case.name, "grid": [case.nx, case.ny, case.nz], "cells": case.cells,
-                   "re_tau": case.re_tau, "tau0": case.tau, "C_s": case.cs, "wall": "wfb",
-                   "storage": args.precision, "les": "MRT + van Driest" if args.les == "mrt" else "BGK",
-                   "layout": "single-lattice AA" if layout == lbm.AA else "two-lattice pull",
-                   "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2 (129 MB): %s %.0f MB lattice%s per step" % (
-                       "one" if layout == lbm.AA else "two", BYTES_PER_LUP[precision] / 2 * case.cells / 1e6,
-                       "" if layout == lbm.AA else "s")},
+        "config": line_config(case, args, world),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
                      "traffic": NCU_TRAFFIC.get((args.workload, args.precision, args.layout, args.les))
