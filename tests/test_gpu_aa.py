@@ -197,3 +197,25 @@ def test_aa_rejects_pipelined_kernel_and_halves_memory():
     lattice = 19 * case.cells * 4
     assert used[lbm.PULL2] >= 2 * lattice
     assert used[lbm.AA] < 1.25 * lattice
+
+
+@pytest.mark.parametrize("case", [SMALL, SMALL.with_(nx=132, ny=5, nz=2), SMALL.with_(nx=4, ny=5, nz=2)],
+                         ids=lambda c: f"{c.nx}x{c.ny}x{c.nz}")
+def test_aa_kernel_switch_mid_run(case):
+    """Switching the kernel form of an FP16 AA channel in the middle of a run,
+    at either phase, keeps the state: each stretch equals the two-lattice
+    channel run with the same forms."""
+    pull = _channel(case, workload.WALL_WFB, lbm.FP16_SHIFTED, lbm.PULL2, lbm.KERNEL_QUAD)
+    aa = _channel(case, workload.WALL_WFB, lbm.FP16_SHIFTED, lbm.AA, lbm.KERNEL_QUAD)
+    t = 0
+    for kernel, n in ((lbm.KERNEL_QUAD, 7), (lbm.KERNEL_PAIR, 5), (lbm.KERNEL_CELL, 4), (lbm.KERNEL_QUAD, 6)):
+        aa.set_kernel(kernel)
+        pull.set_kernel(kernel)
+        aa.step(n)
+        pull.step(n)
+        t += n
+        assert np.array_equal(aa.populations(), pull.populations()), (kernel, t)
+        assert np.array_equal(aa.wall_stress(), pull.wall_stress()), (kernel, t)
+        assert np.array_equal(aa.moments()[1], pull.moments()[1]), (kernel, t)
+    aa.close()
+    pull.close()
