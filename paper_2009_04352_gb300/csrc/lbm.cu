@@ -113,9 +113,12 @@ long long partials_per_plane(const lbm_handle *h)
     return (long long)step_grid(h).x * h->g.nz;
 }
 
-// Launch with programmatic stream serialisation (see pdl_begin in lbm_pair.cuh).
+// Launch with programmatic stream serialisation (see pdl_begin in
+// lbm_pair.cuh) when pdl is set: the grid starts while the previous kernel on
+// the stream drains. Kernels that read the previous step's output through the
+// read-only path launch without it (pull_nc in lbm_device.cuh).
 template <typename... K, typename... A>
-cudaError_t launch_pdl(void (*kernel)(K...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A... args)
+cudaError_t launch_ex(bool pdl, void (*kernel)(K...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A... args)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
@@ -124,10 +127,16 @@ cudaError_t launch_pdl(void (*kernel)(K...), dim3 grid, dim3 block, size_t smem,
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    attr[0].val.programmaticStreamSerializationAllowed = pdl ? 1 : 0;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+template <typename... K, typename... A>
+cudaError_t launch_pdl(void (*kernel)(K...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A... args)
+{
+    return launch_ex(true, kernel, grid, block, smem, s, args...);
 }
 
 template <typename T, int NW, int COLL>
@@ -217,9 +226,17 @@ cudaError_t launch_aa(lbm_handle *h, cudaStream_t s, bool stats)
     const dim3 grid = step_grid(h), block(h->bx);
     void *f = h->f[0];
     if (h->kernel == LBM_KERNEL_QUAD) {
-        // one launch over every row (an interior / wall-row split, as in the
-        // two-lattice step, measured slower for the in-place steps)
         __half *fh = (__half *)f;
+        // The odd step (gather and push through the neighbours, the heavier
+        // kind) calls a separately compiled wall-row tile, which frees the
+        // interior's registers (c4 FP16: 1.96 against 2.11 ms); the even step
+        // is measured faster with the wall layer inline (1.62 against 1.67 ms).
+        // Both are one launch over every row: an interior / wall-row split,
+        // as in the two-lattice step, measured slower in place.
+        if constexpr (LAY == lbm::LAY_AA_ODD)
+            if (!stats && h->g.ny > 2)
+                return launch_pdl(lbm::k_step_quad_aa_rows<false, COLL, LAY>, grid, block, 0, s, fh, h->g, h->p,
+                                  h->tw, h->part);
         return stats ? launch_pdl(lbm::k_step_quad_aa<true, COLL, LAY>, grid, block, 0, s, fh, h->g, h->p, h->tw, h->part)
                      : launch_pdl(lbm::k_step_quad_aa<false, COLL, LAY>, grid, block, 0, s, fh, h->g, h->p, h->tw,
                                   h->part);
@@ -320,9 +337,10 @@ int launch_step_c(lbm_handle *h, cudaStream_t s, int src, bool stats)
         } else {
             const float *af = (const float *)a;
             float *bf = (float *)b;
-            e = stats ? launch_pdl(lbm::k_step_pair<float, true, COLL>, grid, block, 0, s, af, bf, h->g, h->p, h->tw,
+            // read-only loads of the source lattice: no programmatic dependent launch
+            e = stats ? launch_ex(false, lbm::k_step_pair<float, true, COLL>, grid, block, 0, s, af, bf, h->g, h->p, h->tw,
                                    h->part)
-                      : launch_pdl(lbm::k_step_pair<float, false, COLL>, grid, block, 0, s, af, bf, h->g, h->p, h->tw,
+                      : launch_ex(false, lbm::k_step_pair<float, false, COLL>, grid, block, 0, s, af, bf, h->g, h->p, h->tw,
                                    h->part);
         }
     } else if (half) {

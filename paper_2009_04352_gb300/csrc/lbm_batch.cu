@@ -232,7 +232,9 @@ cudaError_t launch_pdl(lbm_batch *b, cudaStream_t s, int cur)
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    // FP32 tiles read the source lattice through the read-only path, which
+    // rules out starting while the previous step drains (pull_nc)
+    attr[0].val.programmaticStreamSerializationAllowed = lbm::pull_nc<T> ? 0 : 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, k_batch_step<T, STATS, COLL>, (const BatchInst *)b->d_inst, b->n, b->tiles,

@@ -22,6 +22,8 @@
 // its own gather read), so the update is in place without races.
 #pragma once
 
+#include <type_traits>
+
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -171,15 +173,24 @@ __device__ __forceinline__ float row_smag(const Phys &p, int y, int ny)
     return p.smag * D * D;
 }
 
+// Loads of the source lattice. The read-only path (ld, __ldg) is valid only
+// for data that no grid writes while the reading grid lives, and the compiler
+// may schedule its loads before griddepcontrol.wait (measured: a four-cell
+// step that read the previous step's output that way, launched while that step
+// drained, read stale populations). So the two-lattice FP32 kernels, whose
+// read-only loads measure faster, launch without programmatic dependent
+// launch, and every other step kernel, launched with it, reads through
+// explicitly coherent loads (ldc, ld.global.ca), which the compiler neither
+// turns into read-only loads nor moves above the wait.
+template <typename T> constexpr bool pull_nc = std::is_same<T, float>::value;
+
 template <typename T> __device__ __forceinline__ float ld(const T *p);
 template <> __device__ __forceinline__ float ld<float>(const float *p) { return __ldg(p); }
 template <> __device__ __forceinline__ float ld<__half>(const __half *p) { return __half2float(__ldg(p)); }
 
-// Coherent loads for the in-place AA steps (the read-only path of ld() is for
-// arrays that no thread writes during the launch).
 template <typename T> __device__ __forceinline__ float ldc(const T *p);
-template <> __device__ __forceinline__ float ldc<float>(const float *p) { return *p; }
-template <> __device__ __forceinline__ float ldc<__half>(const __half *p) { return __half2float(*p); }
+template <> __device__ __forceinline__ float ldc<float>(const float *p) { return __ldca(p); }
+template <> __device__ __forceinline__ float ldc<__half>(const __half *p) { return __half2float(__ldca(p)); }
 
 template <typename T, bool NC> __device__ __forceinline__ float ldx(const T *p) { return NC ? ld<T>(p) : ldc<T>(p); }
 

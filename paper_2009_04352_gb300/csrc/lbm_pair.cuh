@@ -30,15 +30,15 @@ template <> __device__ __forceinline__ float2 ld2<__half>(const __half *p)
     return __half22float2(__ldg(reinterpret_cast<const __half2 *>(p)));
 }
 
-// coherent 2-wide loads for the in-place AA steps
+// coherent 2-wide loads (see pull_nc in lbm_device.cuh)
 template <typename T> __device__ __forceinline__ float2 ldc2(const T *p);
 template <> __device__ __forceinline__ float2 ldc2<float>(const float *p)
 {
-    return *reinterpret_cast<const float2 *>(p);
+    return __ldca(reinterpret_cast<const float2 *>(p));
 }
 template <> __device__ __forceinline__ float2 ldc2<__half>(const __half *p)
 {
-    return __half22float2(*reinterpret_cast<const __half2 *>(p));
+    return __half22float2(__ldca(reinterpret_cast<const __half2 *>(p)));
 }
 
 template <typename T> __device__ __forceinline__ void st2(T *p, float2 v);
@@ -74,7 +74,7 @@ template <typename T, int ROW, int LAY = LAY_PULL>
 __device__ __forceinline__ void gather_pair(const T *src, const Geom &g, int wall, int x0, int y, int z, int zm,
                                             int zp, int lane, float2 (&f)[Q])
 {
-    constexpr bool NC = LAY == LAY_PULL;
+    constexpr bool NC = LAY == LAY_PULL && pull_nc<T>;
     if constexpr (LAY == LAY_AA_EVEN) {
         const T *own = src + ((long long)z * g.ny + y) * g.sx + x0;
 #pragma unroll

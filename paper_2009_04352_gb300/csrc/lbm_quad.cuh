@@ -32,14 +32,14 @@ __device__ __forceinline__ uint32_t f2h(float2 v)
 template <bool NC>
 __device__ __forceinline__ uint2 ld_u2(const __half *p)
 {
-    return NC ? __ldg(reinterpret_cast<const uint2 *>(p)) : *reinterpret_cast<const uint2 *>(p);
+    return NC ? __ldg(reinterpret_cast<const uint2 *>(p)) : __ldca(reinterpret_cast<const uint2 *>(p));
 }
 
 template <bool NC>
 __device__ __forceinline__ uint32_t ld_u16(const __half *p)
 {
     return NC ? (uint32_t)__ldg(reinterpret_cast<const unsigned short *>(p))
-              : (uint32_t)*reinterpret_cast<const unsigned short *>(p);
+              : (uint32_t)__ldca(reinterpret_cast<const unsigned short *>(p));
 }
 
 template <int SH, bool NC = true>
@@ -72,7 +72,7 @@ template <int ROW, int LAY = LAY_PULL>
 __device__ __forceinline__ void gather_quad(const __half *src, const Geom &g, int wall, int x0, int y, int z, int zm,
                                             int zp, int lane, uint2 (&r)[Q])
 {
-    constexpr bool NC = LAY == LAY_PULL;
+    constexpr bool NC = LAY == LAY_PULL && pull_nc<__half>;   // coherent: the quad kernels launch with PDL
     if constexpr (LAY == LAY_AA_EVEN) {
         const __half *own = src + ((long long)z * g.ny + y) * g.sx + x0;
 #pragma unroll
@@ -223,6 +223,9 @@ __device__ __forceinline__ void quad_half(uint2 (&r)[Q], const Phys &p, float sm
 #ifndef LBM_QUAD_AA_MIN_BLOCKS
 #define LBM_QUAD_AA_MIN_BLOCKS 4    // the same for the in-place AA steps with BGK (128 registers)
 #endif
+#ifndef LBM_QUAD_AA_ROWS_MIN_BLOCKS
+#define LBM_QUAD_AA_ROWS_MIN_BLOCKS 4   // AA steps with the wall tile called (k_step_quad_aa_rows)
+#endif
 
 // One tile: the x-quads xb * blockDim.x + threadIdx.x of row (y, z), i.e.
 // cells [4 xb blockDim.x, 4 (xb + 1) blockDim.x). With STATS the block writes
@@ -353,6 +356,32 @@ __global__ void __launch_bounds__(128, COLL == COLL_MRT ? LBM_QUAD_MRT_MIN_BLOCK
     const int y = ROWS == ROWS_INTERIOR ? (int)blockIdx.y + 1 : (int)blockIdx.y, z = blockIdx.z;
     const long long blk = ((long long)y * g.nz + z) * gridDim.x + blockIdx.x;
     quad_tile<STATS, COLL, LAY, ROWS>(f, f, g, p, tw_out, STATS ? part + blk * K_PART : nullptr, blockIdx.x, y, z);
+}
+
+// The wall-row tile of the four-cell AA step, compiled apart from the
+// interior tile (see quad_wall_tile).
+template <bool STATS, int COLL, int LAY>
+__device__ __noinline__ void quad_aa_wall_tile(__half *f, const Geom &g, const Phys &p, float *tw_out,
+                                               double *part_blk, int xb, int y, int z)
+{
+    quad_tile<STATS, COLL, LAY, ROWS_WALL>(f, f, g, p, tw_out, part_blk, xb, y, z);
+}
+
+// The four-cell AA step over every row in one launch, the wall rows' CTAs
+// calling quad_aa_wall_tile, the interior rows running the interior tile
+// inline (its registers are not shaped by the wall layer's code).
+template <bool STATS, int COLL, int LAY>
+__global__ void __launch_bounds__(128, LBM_QUAD_AA_ROWS_MIN_BLOCKS)
+    k_step_quad_aa_rows(__half *f, Geom g, Phys p, float *__restrict__ tw_out, double *__restrict__ part)
+{
+    pdl_begin();
+    const int y = blockIdx.y, z = blockIdx.z;
+    const long long blk = ((long long)y * g.nz + z) * gridDim.x + blockIdx.x;
+    double *pb = STATS ? part + blk * K_PART : nullptr;
+    if (y == 0 || y == g.ny - 1)
+        quad_aa_wall_tile<STATS, COLL, LAY>(f, g, p, tw_out, pb, blockIdx.x, y, z);
+    else
+        quad_tile<STATS, COLL, LAY, ROWS_INTERIOR>(f, f, g, p, tw_out, pb, blockIdx.x, y, z);
 }
 
 }  // namespace lbm
