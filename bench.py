@@ -254,7 +254,8 @@ def time_batch(precision, steps, stream, peak, clocks):
     cases = workload.batch_cases(64, seed=5)
     with torch.cuda.stream(stream):
         b = lbm.Batch(cases, precision=precision, stream=stream.cuda_stream)
-        tuned = autotune.tune_batch(b, steps=3)
+        # one graph chunk per candidate, so that every form is timed as it runs
+        tuned = autotune.tune_batch(b, steps=GRAPH_STEPS)
         for m, c in zip(b.members, cases):
             m.init_channel(workload.u_mean_profile(c), workload.noise_amplitude(c), c.seed)
         b.step(2 * GRAPH_STEPS)

@@ -68,7 +68,7 @@ def _store(path, cache, key, cfg):
     os.replace(tmp, path)
 
 
-def tune_batch(batch, cache_path: str | None = None, steps: int = 3, retune: bool = False) -> dict:
+def tune_batch(batch, cache_path: str | None = None, steps: int = 16, retune: bool = False) -> dict:
     """Apply the cached launch shape for this batch, or time all shapes and cache
     the fastest. Timing advances the members, so call it before initialising them.
     Returns {"threads", "ctas_per_sm", "ms_per_step" (None if from cache), "cached"}."""

@@ -241,30 +241,38 @@ struct MrtPair {
     float2 od[6];          // half-difference change of the diagonal pairs 3 .. 8
 };
 
-__device__ __forceinline__ MrtPair mrt_ghost_pair(const float2 (&hs)[9], const float2 (&hd)[9], float2 f0,
+// s, d: the half sums and differences hs, hd of the pairs, or with PS their
+// doubles (the pair sums and differences): the factors 2 then go exactly into
+// the constants, and the bits are those of the half-sum form.
+template <bool PS>
+__device__ __forceinline__ MrtPair mrt_ghost_pair(const float2 (&s)[9], const float2 (&d)[9], float2 f0,
                                                   float2 rusq, float2 uF, float2 omega, const Phys &p)
 {
     MrtPair m;
-    const float2 A = add2(add2(hs[0], hs[1]), hs[2]);
-    const float2 D = add2(add2(add2(hs[3], hs[4]), add2(hs[5], hs[6])), add2(hs[7], hs[8]));
+    const float2 A = add2(add2(s[0], s[1]), s[2]);                                        // A (PS: 2 A)
+    const float2 D = add2(add2(add2(s[3], s[4]), add2(s[5], s[6])), add2(s[7], s[8]));   // D (PS: 2 D)
+    const float2 D2 = PS ? D : add2(D, D);
     const float2 ke = fma2(omega, bc(p.mrt_a[MRT_E]), bc(p.mrt_b[MRT_E]));
     const float2 kp = fma2(omega, bc(p.mrt_a[MRT_EPS]), bc(p.mrt_b[MRT_EPS]));
-    const float2 kq = fma2(omega, bc(p.mrt_a[MRT_Q]), bc(p.mrt_b[MRT_Q]));
-    const float2 km = fma2(omega, bc(p.mrt_a[MRT_M]), bc(p.mrt_b[MRT_M]));
+    // with PS, C_q and C_m take half of their brackets' doubled partial sums
+    const float hq = PS ? 0.5f : 1.f;
+    const float2 kq = fma2(omega, bc(hq * p.mrt_a[MRT_Q]), bc(hq * p.mrt_b[MRT_Q]));
+    const float2 km = fma2(omega, bc(hq * p.mrt_a[MRT_M]), bc(hq * p.mrt_b[MRT_M]));
     const float2 du = sub2(rusq, uF);
-    const float2 ce = mul2(ke, sub2(sub2(add2(D, D), f0), du));
-    const float2 cp = mul2(kp, fma2(bc(9.f), f0, fma2(bc(-14.f), A, fma2(bc(-4.f), D, mul2(bc(5.5f), du)))));
+    const float2 ce = mul2(ke, sub2(sub2(D2, f0), du));
+    const float2 cp = mul2(kp, fma2(bc(9.f), f0, fma2(bc(PS ? -7.f : -14.f), A,
+                                                      fma2(bc(PS ? -2.f : -4.f), D, mul2(bc(5.5f), du)))));
     m.ea = fma2(bc(-11.f), ce, mul2(bc(-4.f), cp));
     m.ed = fma2(bc(8.f), ce, cp);
     m.er = fma2(bc(-30.f), ce, mul2(bc(12.f), cp));
     // pairs 3..8: first members (1,1,0), (1,0,1), (0,1,1), (1,-1,0), (1,0,-1),
     // (0,1,-1); the q and m brackets share their partial sums
-    const float2 sxa = add2(hd[3], hd[6]), sxb = add2(hd[4], hd[7]);   // q_x = sxa + sxb - 2 hd_x, m_x = sxa - sxb
-    const float2 sya = add2(hd[5], hd[8]), syb = sub2(hd[3], hd[6]);   // q_y = sya + syb - 2 hd_y, m_y = sya - syb
-    const float2 sza = sub2(hd[4], hd[7]), szb = sub2(hd[5], hd[8]);   // q_z = sza + szb - 2 hd_z, m_z = sza - szb
-    m.cq[0] = mul2(kq, fma2(bc(-2.f), hd[0], add2(sxa, sxb)));
-    m.cq[1] = mul2(kq, fma2(bc(-2.f), hd[1], add2(sya, syb)));
-    m.cq[2] = mul2(kq, fma2(bc(-2.f), hd[2], add2(sza, szb)));
+    const float2 sxa = add2(d[3], d[6]), sxb = add2(d[4], d[7]);   // q_x = sxa + sxb - 2 hd_x, m_x = sxa - sxb
+    const float2 sya = add2(d[5], d[8]), syb = sub2(d[3], d[6]);   // q_y = sya + syb - 2 hd_y, m_y = sya - syb
+    const float2 sza = sub2(d[4], d[7]), szb = sub2(d[5], d[8]);   // q_z = sza + szb - 2 hd_z, m_z = sza - szb
+    m.cq[0] = mul2(kq, fma2(bc(-2.f), d[0], add2(sxa, sxb)));
+    m.cq[1] = mul2(kq, fma2(bc(-2.f), d[1], add2(sya, syb)));
+    m.cq[2] = mul2(kq, fma2(bc(-2.f), d[2], add2(sza, szb)));
     const float2 cmx = mul2(km, sub2(sxa, sxb)), cmy = mul2(km, sub2(sya, syb)), cmz = mul2(km, sub2(sza, szb));
     // pair 3 / 6: (Cq_x + Cm_x) +/- (Cq_y - Cm_y); 4 / 7: (Cq_x - Cm_x) +/- (Cq_z + Cm_z);
     // 5 / 8: (Cq_y + Cm_y) +/- (Cq_z - Cm_z)
@@ -297,39 +305,59 @@ __device__ __forceinline__ float2 mrt_odd_add(const MrtPair &m, int k, float2 dd
 // Only the half sums and differences s/2, d/2 are kept through the collision
 // (the new populations are their sum and difference), which keeps 18 fewer
 // values live.
-template <int COLL = COLL_BGK, bool EXACT_W = false>
+//
+// PS selects how the pairs enter: the half sums and differences hs = s/2,
+// hd = d/2 (PS false), or s and d themselves (PS true), every later use taking
+// the 1/2 into a power-of-two constant or a doubling it would otherwise need.
+// Halving commutes with rounding, so both forms compute the same bits; PS
+// saves 28 packed operations per pair, and each kernel takes the form that
+// measured faster with its register budget: PS_DEFAULT for the two-lattice
+// steps (FP32 BGK: +1.7% on c4; FP16 MRT: +2.1% on c3; FP32 MRT -0.3%, FP16
+// BGK two-cell not timed faster), the half sums in the in-place AA pair steps
+// (FP32 c3: 42.3 against 41.2 GLUPS), and per step kind in the four-cell
+// kernels (quad_half). The update stores the new half values hs' = hs + de,
+// hd' = hd + dd in s and d.
+template <int COLL, bool EXACT_W>
+constexpr bool PS_DEFAULT = EXACT_W != (COLL == COLL_MRT);
+
+template <int COLL = COLL_BGK, bool EXACT_W = false, bool PS = PS_DEFAULT<COLL, EXACT_W>>
 __device__ __forceinline__ PairState collide_pair(float2 (&f)[Q], const Phys &p, float smag)
 {
     PairState c;
-    // half sums and half differences of the pairs: f_a = hs + hd, f_b = hs - hd
-    float2 hs[9], hd[9];
+    float2 s[9], d[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-        hs[k] = mul2(bc(0.5f), add2(f[2 * k + 1], f[2 * k + 2]));
-        hd[k] = mul2(bc(0.5f), sub2(f[2 * k + 1], f[2 * k + 2]));
+        s[k] = add2(f[2 * k + 1], f[2 * k + 2]);
+        d[k] = sub2(f[2 * k + 1], f[2 * k + 2]);
+        if constexpr (!PS) {
+            s[k] = mul2(bc(0.5f), s[k]);
+            d[k] = mul2(bc(0.5f), d[k]);
+        }
     }
-    // doubling by addition (exact) keeps constants out of the packed ops
-    const float2 shs = add2(add2(add2(hs[0], hs[1]), add2(hs[2], hs[3])),
-                            add2(add2(hs[4], hs[5]), add2(add2(hs[6], hs[7]), hs[8])));
-    const float2 drho = add2(add2(shs, shs), f[0]);
-    float2 jx = add2(add2(hd[0], hd[3]), add2(add2(hd[4], hd[6]), hd[7]));
-    float2 jy = add2(add2(hd[1], hd[3]), add2(sub2(hd[5], hd[6]), hd[8]));
-    float2 jz = sub2(add2(add2(hd[2], hd[4]), hd[5]), add2(hd[7], hd[8]));
-    jx = add2(jx, jx);
-    jy = add2(jy, jy);
-    jz = add2(jz, jz);
-    float2 pxx = add2(add2(hs[0], hs[3]), add2(add2(hs[4], hs[6]), hs[7]));
-    float2 pyy = add2(add2(hs[1], hs[3]), add2(add2(hs[5], hs[6]), hs[8]));
-    float2 pzz = add2(add2(hs[2], hs[4]), add2(add2(hs[5], hs[7]), hs[8]));
-    float2 pxy = sub2(hs[3], hs[6]);
-    float2 pxz = sub2(hs[4], hs[7]);
-    float2 pyz = sub2(hs[5], hs[8]);
-    pxx = add2(pxx, pxx);
-    pyy = add2(pyy, pyy);
-    pzz = add2(pzz, pzz);
-    pxy = add2(pxy, pxy);
-    pxz = add2(pxz, pxz);
-    pyz = add2(pyz, pyz);
+    // without PS, doubling by addition (exact) keeps constants out of the packed ops
+    const float2 ss = add2(add2(add2(s[0], s[1]), add2(s[2], s[3])),
+                           add2(add2(s[4], s[5]), add2(add2(s[6], s[7]), s[8])));
+    const float2 drho = add2(PS ? ss : add2(ss, ss), f[0]);
+    float2 jx = add2(add2(d[0], d[3]), add2(add2(d[4], d[6]), d[7]));
+    float2 jy = add2(add2(d[1], d[3]), add2(sub2(d[5], d[6]), d[8]));
+    float2 jz = sub2(add2(add2(d[2], d[4]), d[5]), add2(d[7], d[8]));
+    float2 pxx = add2(add2(s[0], s[3]), add2(add2(s[4], s[6]), s[7]));
+    float2 pyy = add2(add2(s[1], s[3]), add2(add2(s[5], s[6]), s[8]));
+    float2 pzz = add2(add2(s[2], s[4]), add2(add2(s[5], s[7]), s[8]));
+    float2 pxy = sub2(s[3], s[6]);
+    float2 pxz = sub2(s[4], s[7]);
+    float2 pyz = sub2(s[5], s[8]);
+    if constexpr (!PS) {
+        jx = add2(jx, jx);
+        jy = add2(jy, jy);
+        jz = add2(jz, jz);
+        pxx = add2(pxx, pxx);
+        pyy = add2(pyy, pyy);
+        pzz = add2(pzz, pzz);
+        pxy = add2(pxy, pxy);
+        pxz = add2(pxz, pxz);
+        pyz = add2(pyz, pyz);
+    }
 
     c.rho = add2(bc(1.f), drho);
     const float2 idev = make_float2(-drho.x / c.rho.x, -drho.y / c.rho.y);   // 1/rho - 1
@@ -373,14 +401,14 @@ __device__ __forceinline__ PairState collide_pair(float2 (&f)[Q], const Phys &p,
     const float2 uF = fma2(ux, bc(p.Fx), fma2(uy, bc(p.Fy), mul2(uz, bc(p.Fz))));
     // MRT: corrections of the ghost groups (zero cost for BGK)
     MrtPair mg;
-    if constexpr (COLL == COLL_MRT) mg = mrt_ghost_pair(hs, hd, f[0], mul2(rho, usq), uF, omega, p);
+    if constexpr (COLL == COLL_MRT) mg = mrt_ghost_pair<PS>(s, d, f[0], mul2(rho, usq), uF, omega, p);
     if constexpr (EXACT_W) {
     // BGK with the weights scaled by 36 (36 w = 12 rest, 2 axis, 1 diagonal:
     // exact) and 1/36 folded into the rate, o36 = omega / 36. Per pair, with
     // W = 36 w, the non-equilibrium difference is formed before the rate
     // multiplies it, and the odd part uses rho (e.u) = e.(j + F/2) directly:
-    //   ne = 36 (feq_even - hs) = W (S0 + 9/2 rho (e.u)^2) - 36 hs
-    //   nd = 36 (feq_odd - hd)  = 3 W (e.j) + 3 W (e.F) / 2 - 36 hd
+    //   ne = 36 (feq_even - hs) = W (S0 + 9/2 rho (e.u)^2) - 36 hs   (36 hs = 18 s)
+    //   nd = 36 (feq_odd - hd)  = 3 W (e.j) + 3 W (e.F) / 2 - 36 hd   (36 hd = 18 d)
     //   de = o36 ne + W gk (9 (e.u)(e.F) - 3 u.F) / 36,  dd = o36 nd + W gk 3 (e.F) / 36
     // and the rest population its own update 36 (feq_0 - f_0) = 12 S0 - 36 f_0.
     // The axis pairs take the momentum residual F/2 - sum e dd (zero in exact
@@ -415,8 +443,8 @@ __device__ __forceinline__ PairState collide_pair(float2 (&f)[Q], const Phys &p,
         const float W3 = axis ? 6.f : 3.f;    // 3 W
         const float2 eu = eus[k];
         const float2 WeF = bc(p.WeF[k]);      // 36 w (e.F)
-        const float2 ne = fma2(mul2(axis ? r45a : r45, eu), eu, fma2(bc(-36.f), hs[k], axis ? S0a : S0));
-        const float2 nd = fma2(bc(W3), ejs[k], fma2(bc(-36.f), hd[k], mul2(bc(1.5f), WeF)));
+        const float2 ne = fma2(mul2(axis ? r45a : r45, eu), eu, fma2(bc(PS ? -18.f : -36.f), s[k], axis ? S0a : S0));
+        const float2 nd = fma2(bc(W3), ejs[k], fma2(bc(PS ? -18.f : -36.f), d[k], mul2(bc(1.5f), WeF)));
         float2 de = fma2(o36, ne, fma2(mul2(g9, WeF), eu, axis ? mgua : mgu));
         float2 dd = fma2(o36, nd, mul2(g3, WeF));
         if constexpr (COLL == COLL_MRT) {
@@ -429,16 +457,16 @@ __device__ __forceinline__ PairState collide_pair(float2 (&f)[Q], const Phys &p,
         else if (k > 1 && ey_of(a)) my = ey_of(a) > 0 ? add2(my, dd) : sub2(my, dd);
         if (k == 2) mz = dd;
         else if (k > 2 && ez_of(a)) mz = ez_of(a) > 0 ? add2(mz, dd) : sub2(mz, dd);
-        hs[k] = add2(hs[k], de);
-        hd[k] = add2(hd[k], dd);
+        s[k] = PS ? fma2(bc(0.5f), s[k], de) : add2(s[k], de);
+        d[k] = PS ? fma2(bc(0.5f), d[k], dd) : add2(d[k], dd);
     }
-    hd[0] = add2(hd[0], sub2(bc(p.hF[0]), mx));
-    hd[1] = add2(hd[1], sub2(bc(p.hF[1]), my));
-    hd[2] = add2(hd[2], sub2(bc(p.hF[2]), mz));
+    d[0] = add2(d[0], sub2(bc(p.hF[0]), mx));
+    d[1] = add2(d[1], sub2(bc(p.hF[1]), my));
+    d[2] = add2(d[2], sub2(bc(p.hF[2]), mz));
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-        f[2 * k + 1] = add2(hs[k], hd[k]);
-        f[2 * k + 2] = sub2(hs[k], hd[k]);
+        f[2 * k + 1] = add2(s[k], d[k]);
+        f[2 * k + 2] = sub2(s[k], d[k]);
     }
     return c;
     } else {
@@ -446,7 +474,7 @@ __device__ __forceinline__ PairState collide_pair(float2 (&f)[Q], const Phys &p,
     // of the update are then corrected on the axis pairs and the rest
     // population (the storage form of FP16, whose rounding dominates)
     const float2 gk = fma2(bc(-0.5f), omega, bc(1.f));
-    const float2 nw = mul2(bc(-1.f), omega);                               // -omega
+    const float2 nw = mul2(bc(PS ? -0.5f : -1.f), omega);                  // -omega (PS: -omega / 2)
     const float2 S0 = fma2(bc(-1.5f), mul2(rho, usq), drho);
     const float2 oS = sub2(mul2(omega, S0), mul2(mul2(bc(3.f), gk), uF));  // omega S0 - 3 gk u.F
     const float2 oR45 = mul2(omega, mul2(bc(4.5f), rho));                // 4.5 omega rho
@@ -468,9 +496,9 @@ __device__ __forceinline__ PairState collide_pair(float2 (&f)[Q], const Phys &p,
         const float2 eu = eus[k];
         const float2 eF = bc(p.weF[k]);   // w e.F
         const float2 Gk = mul2(g9, eF), Hk = mul2(g3, eF);
-        // with s = 2 hs and d = 2 hd: -omega s / 2 = -omega hs
-        float2 de = fma2(nw, hs[k], fma2(fma2(axis ? Aa : Ad, eu, Gk), eu, axis ? Ca : Cd));
-        float2 dd = fma2(nw, hd[k], fma2(axis ? Da : Dd, eu, Hk));
+        // -omega hs (= (-omega / 2) s exactly)
+        float2 de = fma2(nw, s[k], fma2(fma2(axis ? Aa : Ad, eu, Gk), eu, axis ? Ca : Cd));
+        float2 dd = fma2(nw, d[k], fma2(axis ? Da : Dd, eu, Hk));
         if constexpr (COLL == COLL_MRT) {
             de = add2(de, axis ? mg.ea : mg.ed);
             dd = mrt_odd_add(mg, k, dd);
@@ -484,19 +512,19 @@ __device__ __forceinline__ PairState collide_pair(float2 (&f)[Q], const Phys &p,
         if (k == 2) mz = dd;
         else if (k > 2 && ez_of(a)) mz = ez_of(a) > 0 ? add2(mz, dd) : sub2(mz, dd);
         // the pair's new half sum and half difference (delta_a = de + dd, delta_b = de - dd)
-        hs[k] = add2(hs[k], de);
-        hd[k] = add2(hd[k], dd);
+        s[k] = PS ? fma2(bc(0.5f), s[k], de) : add2(s[k], de);
+        d[k] = PS ? fma2(bc(0.5f), d[k], dd) : add2(d[k], dd);
     }
     // exact momentum F and mass 0 of the update (see collide()): the axis pairs
     // take the momentum residual, the rest population the mass residual
-    hd[0] = add2(hd[0], sub2(bc(p.hF[0]), mx));
-    hd[1] = add2(hd[1], sub2(bc(p.hF[1]), my));
-    hd[2] = add2(hd[2], sub2(bc(p.hF[2]), mz));
+    d[0] = add2(d[0], sub2(bc(p.hF[0]), mx));
+    d[1] = add2(d[1], sub2(bc(p.hF[1]), my));
+    d[2] = add2(d[2], sub2(bc(p.hF[2]), mz));
     f[0] = sub2(f[0], add2(mass, mass));
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-        f[2 * k + 1] = add2(hs[k], hd[k]);
-        f[2 * k + 2] = sub2(hs[k], hd[k]);
+        f[2 * k + 1] = add2(s[k], d[k]);
+        f[2 * k + 2] = sub2(s[k], d[k]);
     }
     return c;
     }
@@ -574,7 +602,8 @@ __device__ __forceinline__ void pair_tile(const T *src, T *dst, const Geom &g, c
             *t = make_float4(twx.x, twz.x, twx.y, twz.y);
         }
     } else {
-        c = collide_pair<COLL, sizeof(T) == 4>(f, p, row_smag(p, y, g.ny));
+        c = collide_pair<COLL, sizeof(T) == 4, LAY == LAY_PULL && PS_DEFAULT<COLL, sizeof(T) == 4>>(
+            f, p, row_smag(p, y, g.ny));
     }
 
     if (ROWS != ROWS_INTERIOR && !node_row && (y == 0 || y == g.ny - 1)) {

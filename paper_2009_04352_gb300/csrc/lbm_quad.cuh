@@ -182,14 +182,17 @@ __device__ __forceinline__ void push_quad(__half *dst, const Geom &g, int wall, 
 }
 
 // Collision (and wall layer) of one packed pair held in word H of the quad.
-template <int H, bool STATS, int COLL>
+// The pair-sum form of collide_pair (PS, same bits) measured faster for MRT
+// and for the AA even step, slower for the BGK pull and AA odd steps, whose
+// register allocation it worsens (c4: 72.6 against 79.8 GLUPS pull).
+template <int H, bool STATS, int COLL, int LAY>
 __device__ __forceinline__ void quad_half(uint2 (&r)[Q], const Phys &p, float smag, bool wall_row, bool bottom,
                                           float4 &tw, float (&v)[K_ACC], bool valid)
 {
     float2 f[Q];
 #pragma unroll
     for (int a = 0; a < Q; ++a) f[a] = h2f(H ? r[a].y : r[a].x);
-    const PairState c = collide_pair<COLL>(f, p, smag);
+    const PairState c = collide_pair<COLL, false, COLL == COLL_MRT || LAY == LAY_AA_EVEN>(f, p, smag);
     float2 twx = bc(0.f), twz = bc(0.f);
     if (wall_row) {
         wall_layer_pair(f, c, p, bottom, twx, twz);
@@ -246,8 +249,8 @@ __device__ __forceinline__ void quad_finish(uint2 (&r)[Q], __half *dst, const Ge
     if (STATS) stats_zero(v);
     float4 twa = make_float4(0.f, 0.f, 0.f, 0.f), twb = twa;
     const float smag = row_smag(p, y, g.ny);
-    quad_half<0, STATS, COLL>(r, p, smag, wall_row, y == 0, twa, v, valid);
-    quad_half<1, STATS, COLL>(r, p, smag, wall_row, y == 0, twb, v, valid);
+    quad_half<0, STATS, COLL, LAY>(r, p, smag, wall_row, y == 0, twa, v, valid);
+    quad_half<1, STATS, COLL, LAY>(r, p, smag, wall_row, y == 0, twb, v, valid);
     if (valid && wall_row) {
         float4 *t = reinterpret_cast<float4 *>(reinterpret_cast<float2 *>(tw_out) +
                                                ((long long)((y == 0 ? 0 : 1) * g.nz + z) * g.nx + x0));
