@@ -45,8 +45,8 @@ SAMPLE_CELLS = 2_100_000      # cells of the bounded oracle sample (a z-slab of 
 # z-slab of the same channel and scaled by its cell count (traffic per cell
 # does not depend on nz). Absent keys report null.
 NCU_TRAFFIC = {
-    # k_step_pair<float>, 1024x256x16 slab: 598.4 MB per launch (142.7 B/cell) x 32
-    ("c4", "fp32", "pull", "bgk"): 19.149e9,
+    # k_step_pair<float>, 1024x256x16 slab: 597.5 MB per launch (142.5 B/cell) x 32
+    ("c4", "fp32", "pull", "bgk"): 19.121e9,
 }
 
 
