@@ -6,7 +6,8 @@ friction velocity and the first-layer y1+ distribution (Fig. 7).
 
 Grids are the paper's Table 1 cases (domain 2 pi D x 2D x pi D, D/dx = 20,
 40 or 80 at Re_tau 640 and 2003); the LES operator is the paper's (MRT,
-Smagorinsky C_s = 0.1, van Driest damping with A+ = 26); lattice parameters
+Smagorinsky C_s = 0.1, van Driest damping with A+ = 26, or none with
+--a-plus 0); lattice parameters
 follow the synthetic-workload recipe of workload.py (U_c = 0.04). Time is
 counted in T = D / u_tau as in Sec. 3.1: statistics are accumulated from
 t_spin T to t_end T. Results are normalised with D and the theoretical u_tau,
@@ -53,14 +54,14 @@ def table1_case(name: str, wall: str, y1: float, seed: int = 11, law: int = 0) -
 
 
 def run(case: workload.ChannelCase, t_spin: float, t_end: float, samples_per_t: float = 10.0,
-        snapshots: int = 24, precision: int = 0, stream=None) -> dict:
+        snapshots: int = 24, precision: int = 0, stream=None, a_plus: float = A_PLUS) -> dict:
     from . import lbm
     T = case.half_height / case.u_tau
     n_spin = int(round(t_spin * T))
     n_end = int(round(t_end * T))
     every = max(1, int(round(T / samples_per_t)))
     ch = lbm.Channel.from_case(case, precision=precision, stream=stream)
-    ch.set_les(lbm.COLLISION_MRT, case.u_tau, A_PLUS)
+    ch.set_les(lbm.COLLISION_MRT, case.u_tau if a_plus > 0 else 0.0, a_plus)
     ch.init_channel(workload.u_mean_profile(case), workload.noise_amplitude(case), case.seed)
     t0 = time.perf_counter()
     ch.step(n_spin)
@@ -131,10 +132,13 @@ def main(argv=None) -> int:
     ap.add_argument("--t-end", type=float, default=92.0, help="end of the sampling window, in T")
     ap.add_argument("--samples-per-t", type=float, default=10.0)
     ap.add_argument("--seed", type=int, default=11)
+    ap.add_argument("--a-plus", type=float, default=A_PLUS,
+                    help="van Driest constant A+ (0: no damping of the Smagorinsky length)")
     ap.add_argument("--no-profile", action="store_true", help="omit the profile arrays")
     args = ap.parse_args(argv)
     case = table1_case(args.case, args.wall, args.y1, args.seed, args.law)
-    out = run(case, args.t_spin, args.t_end, args.samples_per_t)
+    out = run(case, args.t_spin, args.t_end, args.samples_per_t, a_plus=args.a_plus)
+    out["a_plus"] = args.a_plus
     if args.no_profile:
         out.pop("profile")
     print(json.dumps(out))
