@@ -1,4 +1,4 @@
-"""Host logic of the validation driver (no GPU): the Table 1 grids and the
+"""Host logic of the validation runner (no GPU): the Table 1 grids and the
 summary statistics, fed with plane sums of known profiles."""
 import math
 
