@@ -140,9 +140,11 @@ typedef enum {
  *         shared-memory ring with bulk asynchronous copies (full/empty
  *         mbarriers, 2-4 stages); nx a multiple of 64 whose rows fit the ring.
  *   QUAD: four cells per thread, 8-byte loads and stores; FP16 storage and nx a
- *         multiple of 4 (halfway walls). With the two-lattice layout and BGK
+ *         multiple of 4. With the two-lattice layout and BGK (or wall nodes)
  *         a step is two launches, the interior rows and then the two wall
- *         rows, the latter with the two-cell tile (the same bits).
+ *         rows, the latter with the two-cell tile (the same bits); with MRT
+ *         and halfway walls one launch whose wall rows call a separately
+ *         compiled four-cell wall tile.
  *   AUTO: QUAD where allowed, else PAIR for even nx, else CELL. */
 typedef enum {
     LBM_KERNEL_AUTO = 0,

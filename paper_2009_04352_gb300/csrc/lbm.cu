@@ -61,15 +61,17 @@ int select_kernel(lbm_handle *h, int kernel)
 {
     const bool even = (h->g.nx % 2) == 0;
     const bool seg = (h->g.nx % 64) == 0;
-    const bool node = h->p.wall == lbm::WALL_NODE;   // wall nodes: the cell and pair forms only
-    const bool quad = (h->g.nx % 4) == 0 && h->precision == LBM_FP16_SHIFTED && !node;
+    // wall nodes: every form but the row pipeline (the four-cell step runs its
+    // node rows with the two-cell wall tile)
+    const bool node = h->p.wall == lbm::WALL_NODE;
+    const bool quad = (h->g.nx % 4) == 0 && h->precision == LBM_FP16_SHIFTED;
     // AUTO: FP16 storage with nx a multiple of 4 runs the four-cell kernel, else
     // the two-cell kernel where nx is even, else the one-cell kernel (measured
     // fastest in that order on GB300 for every benchmark grid)
     if (kernel == LBM_KERNEL_AUTO) kernel = quad ? LBM_KERNEL_QUAD : (even ? LBM_KERNEL_PAIR : LBM_KERNEL_CELL);
     if (kernel == LBM_KERNEL_PAIR && !even) return fail(LBM_ERR_ARG, "two-cell kernel needs an even nx");
     if (kernel == LBM_KERNEL_QUAD && !quad)
-        return fail(LBM_ERR_ARG, "four-cell kernel needs FP16 storage, nx a multiple of 4 and halfway walls");
+        return fail(LBM_ERR_ARG, "four-cell kernel needs FP16 storage and nx a multiple of 4");
     if (kernel == LBM_KERNEL_TMA && node) return fail(LBM_ERR_ARG, "the pipelined kernel has no wall-node form");
     if (kernel == LBM_KERNEL_TMA && !seg) return fail(LBM_ERR_ARG, "pipelined kernel needs nx a multiple of 64");
     if (kernel == LBM_KERNEL_TMA && h->layout == LBM_AA)
@@ -302,7 +304,7 @@ int launch_step_c(lbm_handle *h, cudaStream_t s, int src, bool stats)
         __half *bh = (__half *)b;
         bool fused = false;
         if constexpr (COLL == lbm::COLL_MRT) {
-            fused = h->g.ny > 2;
+            fused = h->g.ny > 2 && h->p.wall != lbm::WALL_NODE;   // the called wall tile has no node form
             if (fused)
                 e = stats ? launch_pdl(lbm::k_step_quad_rows<true, COLL>, grid, block, 0, s, ah, bh, h->g, h->p,
                                        h->tw, h->part)
@@ -310,14 +312,13 @@ int launch_step_c(lbm_handle *h, cudaStream_t s, int src, bool stats)
                                        h->tw, h->part);
         }
         if (!fused) {
-            if constexpr (COLL == lbm::COLL_BGK) {
-                if (h->g.ny > 2) {
-                    const dim3 gi(grid.x, h->g.ny - 2, grid.z);
-                    e = stats ? launch_pdl(lbm::k_step_quad<true, COLL, lbm::ROWS_INTERIOR>, gi, block, 0, s, ah, bh,
-                                           h->g, h->p, h->tw, h->part)
-                              : launch_pdl(lbm::k_step_quad<false, COLL, lbm::ROWS_INTERIOR>, gi, block, 0, s, ah,
-                                           bh, h->g, h->p, h->tw, h->part);
-                }
+            // the interior rows (BGK, or MRT with wall nodes), then the wall rows
+            if (h->g.ny > 2) {
+                const dim3 gi(grid.x, h->g.ny - 2, grid.z);
+                e = stats ? launch_pdl(lbm::k_step_quad<true, COLL, lbm::ROWS_INTERIOR>, gi, block, 0, s, ah, bh,
+                                       h->g, h->p, h->tw, h->part)
+                          : launch_pdl(lbm::k_step_quad<false, COLL, lbm::ROWS_INTERIOR>, gi, block, 0, s, ah, bh,
+                                       h->g, h->p, h->tw, h->part);
             }
             const dim3 gw(grid.x, 2, grid.z), bw(2 * h->bx);
             if (e == cudaSuccess)

@@ -65,9 +65,10 @@ __device__ __forceinline__ uint2 row_quad(const __half *row, int x0, int nx, int
 }
 
 // Gather of the quad (streaming with the wall reflection of src_offset); the
-// layouts as in gather_pair of lbm_pair.cuh. The four-cell form serves halfway
-// walls only (wall nodes run the one- and two-cell forms), so the bounce-back
-// map is taken for WALL_BB alone.
+// layouts as in gather_pair of lbm_pair.cuh. The four-cell wall rows serve
+// halfway walls only (with wall nodes the step runs its interior rows with the
+// four-cell tile and the node rows with the two-cell wall tile), so the
+// bounce-back map is taken for WALL_BB alone.
 template <int ROW, int LAY = LAY_PULL>
 __device__ __forceinline__ void gather_quad(const __half *src, const Geom &g, int wall, int x0, int y, int z, int zm,
                                             int zp, int lane, uint2 (&r)[Q])

@@ -1,6 +1,7 @@
-"""The full-way (wall-node) WFB on the GPU against the oracle: the one-cell and
-two-cell kernels, FP32 and FP16 storage, ragged grids down to one fluid layer,
-the batch, and the kernel forms and layouts that have no wall-node form."""
+"""The full-way (wall-node) WFB on the GPU against the oracle: the one-, two-
+and four-cell kernels (the four-cell step runs its node rows with the two-cell
+wall tile), FP32 and FP16 storage, BGK and MRT, ragged grids down to one fluid
+layer, the batch, and the kernel form and layout that have no wall-node form."""
 import numpy as np
 import pytest
 
@@ -37,8 +38,11 @@ def _channel(case, precision, kernel):
     return ch
 
 
-@pytest.mark.parametrize("kernel", [lbm.KERNEL_PAIR, lbm.KERNEL_CELL])
-@pytest.mark.parametrize("precision", [lbm.FP32, lbm.FP16_SHIFTED])
+FORMS = [(lbm.FP32, lbm.KERNEL_PAIR), (lbm.FP32, lbm.KERNEL_CELL), (lbm.FP16_SHIFTED, lbm.KERNEL_PAIR),
+         (lbm.FP16_SHIFTED, lbm.KERNEL_CELL), (lbm.FP16_SHIFTED, lbm.KERNEL_QUAD)]
+
+
+@pytest.mark.parametrize("precision,kernel", FORMS)
 def test_wall_node_parity_100_steps(precision, kernel):
     ref = reference(NODE_C1, (100,))[100]
     fl = floors(NODE_C1, (100,), precision)[100]
@@ -49,8 +53,24 @@ def test_wall_node_parity_100_steps(precision, kernel):
     ch.close()
 
 
-@pytest.mark.parametrize("kernel", [lbm.KERNEL_PAIR, lbm.KERNEL_CELL])
-@pytest.mark.parametrize("precision", [lbm.FP32, lbm.FP16_SHIFTED])
+@pytest.mark.parametrize("precision,kernel", FORMS)
+def test_wall_node_mrt_parity_100_steps(precision, kernel):
+    """The paper's LES operator (MRT, Smagorinsky, van Driest damping with the
+    distance to the nearer wall node) with the full-way WFB, against the
+    oracle."""
+    les = (lbm.COLLISION_MRT, NODE_C1.u_tau, 26.0)
+    ref = reference(NODE_C1, (100,), None, les)[100]
+    fl = floors(NODE_C1, (100,), precision, None, les)[100]
+    ch = lbm.Channel.from_case(NODE_C1, precision=precision)
+    ch.set_kernel(kernel)
+    ch.set_les(*les)
+    ch.init_channel(workload.u_mean_profile(NODE_C1), workload.noise_amplitude(NODE_C1), NODE_C1.seed)
+    ch.step(100)
+    check_state(ch, ref, fl, precision, NODE_C1.wall, populations=True, tag=("mrt", kernel))
+    ch.close()
+
+
+@pytest.mark.parametrize("precision,kernel", FORMS)
 def test_wall_node_log_region_100_steps(precision, kernel):
     """Wall law in its log region (R ~ 500) at tau0 near 1/2, where the
     storage rounding of a weakly damped FP16 run accumulates: every quantity
@@ -102,12 +122,29 @@ def test_wall_node_batch_member_equals_channel(precision):
     b.close()
 
 
+@pytest.mark.parametrize("precision", [lbm.FP16_SHIFTED, lbm.FP32])
+def test_wall_node_mrt_forms_agree(precision):
+    """MRT + van Driest on wall nodes: every kernel form the grid allows gives
+    the same bits (the four-cell step with the two-cell node rows included)."""
+    forms = [lbm.KERNEL_PAIR] + ([lbm.KERNEL_QUAD] if precision == lbm.FP16_SHIFTED else [])
+    out = []
+    for k in forms:
+        ch = lbm.Channel.from_case(NODE, precision=precision)
+        ch.set_kernel(k)
+        ch.set_les(lbm.COLLISION_MRT, NODE.u_tau, 26.0)
+        ch.init_channel(workload.u_mean_profile(NODE), workload.noise_amplitude(NODE), NODE.seed)
+        ch.step(37)
+        out.append((ch.populations(), ch.wall_stress()))
+        ch.close()
+    for f, tw in out[1:]:
+        assert np.array_equal(f, out[0][0]) and np.array_equal(tw, out[0][1])
+
+
 def test_wall_node_rejects_other_forms():
     ch = lbm.Channel.from_case(NODE, precision=lbm.FP16_SHIFTED)
-    assert ch.kernel == lbm.KERNEL_PAIR          # AUTO does not pick the four-cell form
-    for k in (lbm.KERNEL_QUAD, lbm.KERNEL_TMA):
-        with pytest.raises(lbm.LbmError):
-            ch.set_kernel(k)
+    assert ch.kernel == lbm.KERNEL_QUAD          # AUTO picks the four-cell form
+    with pytest.raises(lbm.LbmError):
+        ch.set_kernel(lbm.KERNEL_TMA)
     ch.close()
     with pytest.raises(lbm.LbmError):
         lbm.Channel.from_case(NODE, layout=lbm.AA)
