@@ -86,12 +86,13 @@ def headline_kernel(case, precision, layout=0):
 
 def launches_per_step(case, precision, layout=0, mrt=False):
     """Step-kernel launches per step: the two-lattice FP16 four-cell form with
-    BGK runs an interior-row launch and a wall-row launch (with MRT one launch
-    whose wall-row CTAs call a separately compiled tile); every other form
-    one."""
+    BGK, or with wall nodes, runs an interior-row launch and a wall-row launch
+    (with MRT and halfway walls one launch whose wall-row CTAs call a
+    separately compiled tile); every other form one."""
     from paper_2009_04352_gb300 import lbm
     quad = precision == lbm.FP16_SHIFTED and case.nx % 4 == 0
-    return 2 if quad and layout == lbm.PULL2 and not mrt and case.ny > 2 else 1
+    node = case.wall == workload.WALL_WFB_NODE
+    return 2 if quad and layout == lbm.PULL2 and (not mrt or node) and case.ny > 2 else 1
 
 
 def sample_case(case, cells=SAMPLE_CELLS):

@@ -122,6 +122,8 @@ def test_bench_launch_and_kernel_bookkeeping():
     assert bench.launches_per_step(c3, lbm.FP16_SHIFTED, lbm.AA) == 1
     assert bench.launches_per_step(c3, lbm.FP16_SHIFTED, mrt=True) == 1   # one launch, wall tile called
     assert bench.launches_per_step(c3.with_(ny=2), lbm.FP16_SHIFTED) == 1
+    node = c3.with_(ny=129, wall=workload.WALL_WFB_NODE)
+    assert bench.launches_per_step(node, lbm.FP16_SHIFTED, mrt=True) == 2     # node rows: two-cell wall launch
     assert bench.headline_kernel(c2, lbm.FP32) == "k_step_pair"
     assert bench.headline_kernel(c3, lbm.FP16_SHIFTED) == "k_step_quad"
     assert bench.headline_kernel(c3, lbm.FP16_SHIFTED, lbm.AA) == "k_step_quad_aa"
