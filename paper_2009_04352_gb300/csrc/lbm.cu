@@ -115,6 +115,10 @@ long long partials_per_plane(const lbm_handle *h)
     return (long long)step_grid(h).x * h->g.nz;
 }
 
+#ifndef LBM_FORK_WALL
+#define LBM_FORK_WALL 1
+#endif
+
 // Launch with programmatic stream serialisation (see pdl_begin in
 // lbm_pair.cuh) when pdl is set: the grid starts while the previous kernel on
 // the stream drains. Kernels that read the previous step's output through the
@@ -272,7 +276,7 @@ cudaError_t launch_aa(lbm_handle *h, cudaStream_t s, bool stats)
 }
 
 template <int COLL>
-int launch_step_c(lbm_handle *h, cudaStream_t s, int src, bool stats)
+int launch_step_c(lbm_handle *h, cudaStream_t s, int src, bool stats, cudaStream_t s_wall)
 {
     const dim3 grid = step_grid(h), block(h->bx);
     const bool half = h->precision == LBM_FP16_SHIFTED;
@@ -322,10 +326,10 @@ int launch_step_c(lbm_handle *h, cudaStream_t s, int src, bool stats)
             }
             const dim3 gw(grid.x, 2, grid.z), bw(2 * h->bx);
             if (e == cudaSuccess)
-                e = stats ? launch_pdl(lbm::k_step_pair_wall<__half, true, COLL>, gw, bw, 0, s, ah, bh, h->g, h->p,
-                                       h->tw, h->part)
-                          : launch_pdl(lbm::k_step_pair_wall<__half, false, COLL>, gw, bw, 0, s, ah, bh, h->g, h->p,
-                                       h->tw, h->part);
+                e = stats ? launch_pdl(lbm::k_step_pair_wall<__half, true, COLL>, gw, bw, 0, s_wall, ah, bh, h->g,
+                                       h->p, h->tw, h->part)
+                          : launch_pdl(lbm::k_step_pair_wall<__half, false, COLL>, gw, bw, 0, s_wall, ah, bh, h->g,
+                                       h->p, h->tw, h->part);
         }
     } else if (h->kernel == LBM_KERNEL_PAIR) {
         if (half) {
@@ -370,10 +374,23 @@ int launch_step_c(lbm_handle *h, cudaStream_t s, int src, bool stats)
     return LBM_OK;
 }
 
-int launch_step(lbm_handle *h, cudaStream_t s, int src, bool stats)
+// One step on stream s; the wall-row launch of a two-launch four-cell step goes
+// to s_wall (s when null).
+int launch_step(lbm_handle *h, cudaStream_t s, int src, bool stats, cudaStream_t s_wall = nullptr)
 {
-    return h->p.collision == lbm::COLL_MRT ? launch_step_c<lbm::COLL_MRT>(h, s, src, stats)
-                                           : launch_step_c<lbm::COLL_BGK>(h, s, src, stats);
+    if (!s_wall) s_wall = s;
+    return h->p.collision == lbm::COLL_MRT ? launch_step_c<lbm::COLL_MRT>(h, s, src, stats, s_wall)
+                                           : launch_step_c<lbm::COLL_BGK>(h, s, src, stats, s_wall);
+}
+
+// Whether a plain step is the two-launch four-cell form (interior rows, then
+// the wall rows with the two-cell tile): both read the source lattice and
+// write disjoint rows of the destination, so inside a graph the wall-row
+// launch is a parallel branch of the step instead of running after it.
+bool two_launch_step(const lbm_handle *h)
+{
+    return h->kernel == LBM_KERNEL_QUAD && h->layout == LBM_PULL2 && h->g.ny > 2 &&
+           (h->p.collision == lbm::COLL_BGK || h->p.wall == lbm::WALL_NODE);
 }
 
 int build_chunk(lbm_handle *h, int start)
@@ -381,8 +398,23 @@ int build_chunk(lbm_handle *h, int start)
     cudaGraph_t graph = nullptr;
     CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
     int rc = LBM_OK;
-    for (int i = 0; i < kGraphSteps && rc == LBM_OK; ++i) rc = launch_step(h, h->cap, start ^ (i & 1), false);
+    const bool fork = LBM_FORK_WALL && two_launch_step(h);
+    cudaError_t ce = cudaSuccess;
+    for (int i = 0; i < kGraphSteps && rc == LBM_OK && ce == cudaSuccess; ++i) {
+        if (fork) {
+            // the step's two launches depend on the whole previous step and
+            // the next step on both of them
+            ce = cudaEventRecord(h->fork, h->cap);
+            if (ce == cudaSuccess) ce = cudaStreamWaitEvent(h->cap_wall, h->fork, 0);
+            if (ce == cudaSuccess) rc = launch_step(h, h->cap, start ^ (i & 1), false, h->cap_wall);
+            if (ce == cudaSuccess && rc == LBM_OK) ce = cudaEventRecord(h->join, h->cap_wall);
+            if (ce == cudaSuccess && rc == LBM_OK) ce = cudaStreamWaitEvent(h->cap, h->join, 0);
+        } else {
+            rc = launch_step(h, h->cap, start ^ (i & 1), false);
+        }
+    }
     cudaError_t e = cudaStreamEndCapture(h->cap, &graph);
+    if (ce != cudaSuccess && rc == LBM_OK) rc = fail(LBM_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ce));
     if (rc != LBM_OK) {
         if (graph) cudaGraphDestroy(graph);
         return rc;
@@ -557,8 +589,11 @@ int lbm_create_handle(lbm_grid g, double tau, double C_s, const double force[3],
         lbm_free_handle(h);
         return rc;
     };
-    if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess)
-        return bail(fail(LBM_ERR_CUDA, "cannot create capture stream"));
+    if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&h->cap_wall, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming) != cudaSuccess)
+        return bail(fail(LBM_ERR_CUDA, "cannot create capture streams"));
     const size_t bytes = (size_t)lbm::Q * plane * elem_size(h);
     h->borrowed = pop0 != nullptr;
     if (h->borrowed) {
@@ -620,6 +655,9 @@ void lbm_free_handle(lbm_handle *h)
     if (h->acc) cudaFree(h->acc);
     if (h->err) cudaFree(h->err);
     if (h->cap) cudaStreamDestroy(h->cap);
+    if (h->cap_wall) cudaStreamDestroy(h->cap_wall);
+    if (h->fork) cudaEventDestroy(h->fork);
+    if (h->join) cudaEventDestroy(h->join);
     delete h;
 }
 

@@ -15,6 +15,8 @@ struct lbm_handle {
     int layout;
     cudaStream_t stream;
     cudaStream_t cap;            // private stream used only for graph capture
+    cudaStream_t cap_wall;       // second capture stream: the wall-row branch of a four-cell step
+    cudaEvent_t fork, join;      // fork and join of that branch inside a capture
     void *f[2];                  // two lattices (AA: f[0] only)
     int cur;                     // PULL2: lattice holding the current state; AA: phase (0 or 1)
     long long step;
