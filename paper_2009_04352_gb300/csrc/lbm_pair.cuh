@@ -655,7 +655,10 @@ __device__ __forceinline__ void pair_tile(const T *src, T *dst, const Geom &g, c
 // Programmatic dependent launch: let the next step's grid start launching once
 // every CTA of this one is running, and wait for the previous grid (whose
 // output this step reads and whose input it overwrites) to complete before
-// touching global memory. Both are no-ops for ordinary launches.
+// touching global memory. Both are no-ops for ordinary launches. The wait
+// orders coherent loads only: read-only loads may be scheduled above it, so a
+// kernel launched this way reads the previous step's output with coherent
+// loads (pull_nc in lbm_device.cuh).
 __device__ __forceinline__ void pdl_begin()
 {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
