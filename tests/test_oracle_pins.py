@@ -739,6 +739,30 @@ def test_walls_mirror_symmetric(oracle_lib, wall):
     assert np.allclose(ta[::-1], tb, rtol=1e-9, atol=1e-20)
 
 
+@pytest.mark.parametrize("wall", [1, 3])
+def test_mrt_van_driest_walls_mirror_symmetric_and_conserve_mass(oracle_lib, wall):
+    """The paper's LES operator (MRT, Smagorinsky, van Driest damping by the
+    distance to the nearer wall) with the halfway and the wall-node WFB:
+    mass is conserved to round-off and the top wall is the mirror image of the
+    bottom one (a damping distance or a wall rule that treats the two walls
+    differently fails)."""
+    nx, ny, nz = 9, 7, 6
+    F = (2.2e-7, 0.0, -1.1e-7)
+    A = _seeded(oracle_lib, nx, ny, nz, wall, force=F, amp=6e-3)
+    A.set_les(1, 0.004, 26.0)
+    f = A.populations()
+    B = oracle_lib.Lattice(nx, ny, nz, 0.52, 0.1, F, wall)
+    B.set_les(1, 0.004, 26.0)
+    B.set_populations(_mirror_y(f))
+    m0 = math.fsum(f.ravel())
+    A.step(6)
+    B.step(6)
+    fa, fb = A.populations(), B.populations()
+    assert abs(math.fsum(fa.ravel()) - m0) <= 1e-12 * m0
+    assert np.max(np.abs(_mirror_y(fa) - fb)) <= 1e-14 * np.max(np.abs(fa))
+    assert np.allclose(A.wall_stress()[::-1], B.wall_stress(), rtol=1e-9, atol=1e-20)
+
+
 def test_wall_node_rest_state_and_ny3(oracle_lib):
     """A channel at rest stays at rest (tau_w = 0 for u_t = 0), and the
     narrowest wall-node channel (one fluid layer) conserves mass."""
